@@ -1,0 +1,191 @@
+/*
+ * lbm.h -- C ABI of the GB300 axisymmetric thermal lattice Boltzmann LES
+ * library (liblbm).
+ *
+ * The library advances one lattice of the double-population model of
+ * Djebali et al. (arXiv:1002.3028): D2Q9 populations f_k for density and
+ * momentum and D2Q4 populations g_k for temperature, Eq. 1, with
+ *   - the macroscopic moments of Eq. 2,
+ *   - the Smagorinsky closed-form relaxation time of Eqs. 3-4 and the
+ *     turbulent diffusivity of Eq. 5,
+ *   - viscosity and diffusivity read from temperature-indexed tables
+ *     (Section 2.3),
+ *   - the axisymmetric source terms F1, F2i, S named under Eq. 1 (Zhou's
+ *     axisymmetric model, the paper's ref. [4]),
+ *   - the inlet profiles of Eq. 7 (Section 2.4) and axis, wall, open and
+ *     outflow boundaries.
+ * Every step is one fused pull-stream + collide kernel on the GPU.
+ *
+ * Conventions (all lattice units, dx = dt = 1):
+ *   x is axial (index i, 0 <= i < nx); r is radial (index j, 0 <= j < nr);
+ *   node j sits at radius r0 + j + 1/2.
+ *   D2Q9 e_k: (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
+ *   D2Q4 e_k: (1,0) (0,1) (-1,0) (0,-1).
+ *   Population arrays exchanged through this header are FP64, laid out
+ *   [k][j][i] (k slowest, i fastest, no padding): 9 f planes, 4 g planes.
+ *   Field arrays are [c][j][i] with c = rho, u_x, u_r, T.
+ *
+ * Threading and streams: a handle may be used from one host thread at a
+ * time.  Every call that takes a stream enqueues its GPU work on that stream
+ * (NULL = the legacy default stream) and returns without synchronising,
+ * unless stated otherwise.  Host arrays passed in are copied before the call
+ * returns; device arrays passed in must stay valid until the enqueued work
+ * has completed.
+ *
+ * Errors: every int-returning call returns LBM_OK (0) or a negative
+ * lbm_status; lbm_last_error() gives a message for the calling thread.
+ * Outputs are left untouched on error.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_lattice lbm_lattice; /* opaque handle */
+typedef void *lbm_stream;               /* a cudaStream_t; NULL = default stream */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID_ARG = -1, /* bad handle, size, boundary kind or table */
+    LBM_ERR_OOM = -2,         /* device allocation failed or caller memory too small */
+    LBM_ERR_CUDA = -3,        /* a CUDA runtime call or a kernel launch failed */
+    LBM_ERR_DIVERGED = -4     /* non-finite or non-positive density / temperature found */
+} lbm_status;
+
+/* storage type of the populations on the device (the arithmetic is FP64
+ * for LBM_F64 and FP32 for the others).  All types store the deviation
+ * from the rest state, f_k - w_k rho0 and g_k - T0/4. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3 } lbm_storage;
+
+typedef enum { LBM_IN_INLET = 0, LBM_IN_PERIODIC = 1 } lbm_bc_in;
+typedef enum { LBM_OUT_OUTFLOW = 0, LBM_OUT_WALL = 1, LBM_OUT_PERIODIC = 2 } lbm_bc_out;
+typedef enum { LBM_TOP_WALL = 0, LBM_TOP_OPEN = 1 } lbm_bc_top;
+typedef enum { LBM_BOTTOM_AXIS = 0, LBM_BOTTOM_WALL = 1 } lbm_bc_bottom;
+
+/*
+ * Lattice description (Section 2.4: a half-plane of nx x nr nodes whose
+ * inlet edge carries the profiles of Eq. 7).
+ *
+ * Boundary rules, applied to every pulled source outside the lattice, the
+ * radial rule before the axial one:
+ *   bottom AXIS   specular mirror (requires r0 == 0);
+ *   bottom/top WALL, outlet WALL
+ *                 half-way bounce-back for f; anti-bounce-back for g holding
+ *                 T_bottom / T_top / T_out;
+ *   top OPEN, outlet OUTFLOW
+ *                 zero-gradient copy of the last row / column, its density
+ *                 shifted back to rho0 along the unit-density equilibrium;
+ *   inlet INLET   equilibrium at the density of the first column, velocity
+ *                 (u_in[j] + noise, 0), temperature T_in[j];
+ *   PERIODIC      wrap (must be set on both axial ends).
+ * noise: xi = noise_amp (2U - 1) on rows with u_in[j] != 0, U the top 53
+ * bits of splitmix64(seed ^ splitmix64(step * 2^20 + j)) / 2^53.
+ * axisym = 0 switches the axisymmetric sources off (the planar model).
+ */
+typedef struct {
+    int32_t nx, nr;      /* 1 <= nx, nr; nx * nr <= 2^31 - 1 */
+    int32_t storage;     /* lbm_storage */
+    int32_t bc_in;       /* lbm_bc_in */
+    int32_t bc_out;      /* lbm_bc_out */
+    int32_t bc_top;      /* lbm_bc_top */
+    int32_t bc_bottom;   /* lbm_bc_bottom */
+    int32_t axisym;      /* 1: axisymmetric sources F1, F2i, S on */
+    double r0;           /* radius of the bottom edge */
+    double rho0, T0;     /* reference density and temperature (rest state) */
+    double Cs;           /* Smagorinsky constant (Eq. 3); 0 = no model */
+    double Pr_t;         /* turbulent Prandtl number (Eq. 5), > 0 */
+    double T_top, T_bottom, T_out; /* wall temperatures */
+    double noise_amp;    /* amplitude of the inlet velocity noise */
+    uint64_t seed;       /* seed of the inlet noise */
+} lbm_desc;
+
+/* Message of the last failed call on this host thread ("" if none). */
+LBM_API const char *lbm_last_error(void);
+
+/* Bytes of device memory a lattice needs (two population buffers plus
+ * tables, 256-byte aligned).  Returns LBM_ERR_INVALID_ARG for a bad desc. */
+LBM_API int lbm_required_bytes(const lbm_desc *d, size_t *bytes);
+
+/*
+ * Create a lattice at rest (rho0, T0, u = 0), step counter 0, inlet
+ * u_in = 0 and T_in = T0, properties nu = alpha = 0.1 on [T0, T0 + 1].
+ *   dev_mem:  caller-owned device memory of at least lbm_required_bytes()
+ *             bytes, 256-byte aligned, or NULL to let the library
+ *             cudaMalloc (and later free) its own.  Caller memory must
+ *             outlive the handle.
+ *   out:      receives the handle; untouched on error.
+ * Synchronises the current device.  Errors: INVALID_ARG, OOM, CUDA.
+ */
+LBM_API int lbm_create(const lbm_desc *d, void *dev_mem, size_t bytes, lbm_lattice **out);
+
+/* Release the handle (and the library's own memory, after synchronising
+ * the device).  NULL is a no-op. */
+LBM_API void lbm_destroy(lbm_lattice *h);
+
+/*
+ * Inlet profiles of Eq. 7: host arrays of nr values, u_in = axial inlet
+ * velocity and T_in = inlet temperature at each row (copied).
+ */
+LBM_API int lbm_set_inlet(lbm_lattice *h, const double *u_in, const double *T_in, int32_t nr,
+                  lbm_stream stream);
+
+/*
+ * Temperature-dependent properties of Section 2.3: n >= 1 host values each
+ * of the lattice viscosity nu and diffusivity alpha on a uniform grid over
+ * [T_lo, T_hi] (n == 1: constants), linearly interpolated, T clamped to the
+ * range.  tau_nu = 1/2 + 3 nu, tau_alpha = 1/2 + 2 alpha (Section 2.1).
+ * Requires n <= 4096, T_hi > T_lo when n > 1, nu > 0 and alpha > 0.
+ */
+LBM_API int lbm_set_properties(lbm_lattice *h, const double *nu, const double *alpha, int32_t n,
+                       double T_lo, double T_hi, lbm_stream stream);
+
+/*
+ * Advance nsteps >= 0 time steps (Eq. 1), one fused kernel launch per step.
+ * Asynchronous; returns LBM_ERR_CUDA if a launch fails.
+ */
+LBM_API int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream);
+
+/* Number of steps taken so far (the time index of the inlet noise). */
+LBM_API int64_t lbm_get_step(const lbm_lattice *h);
+
+/*
+ * Macroscopic fields at the current time: the Eq. 2 moments rho, u_x, u_r,
+ * T of the populations streamed from the stored state.  dev_out is caller
+ * device memory of 4 * nr * nx values of type out_type (LBM_F64 or LBM_F32),
+ * layout [c][j][i].
+ */
+LBM_API int lbm_get_fields(lbm_lattice *h, void *dev_out, int32_t out_type, lbm_stream stream);
+
+/*
+ * Copy the stored post-collision populations out of / into the lattice as
+ * absolute FP64 values: dev_f holds 9 * nr * nx values, dev_g 4 * nr * nx,
+ * both caller device memory, layout [k][j][i].  set_state also sets the
+ * step counter.  Values are rounded to the storage type on the way in.
+ */
+LBM_API int lbm_get_state(lbm_lattice *h, double *dev_f, double *dev_g, lbm_stream stream);
+LBM_API int lbm_set_state(lbm_lattice *h, const double *dev_f, const double *dev_g, int64_t step,
+                  lbm_stream stream);
+
+/*
+ * Launch shape of the step kernel: rows per warp tile (band height, >= 1)
+ * and warps per CTA (1..8).  0 keeps the current value.  Used by the
+ * autotuner; results do not depend on it.
+ */
+LBM_API int lbm_set_launch(lbm_lattice *h, int32_t band_rows, int32_t warps_per_cta);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

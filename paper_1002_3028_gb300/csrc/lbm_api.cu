@@ -1,0 +1,476 @@
+// C ABI of liblbm (declared in include/lbm.h): lattice handles, device
+// memory layout, table uploads and the per-step launch loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(LBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+constexpr int kMaxTable = 4096;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+size_t storage_bytes(int storage)
+{
+    switch (storage) {
+    case LBM_F64: return 8;
+    case LBM_F32: return 4;
+    case LBM_F16: return 2;
+    case LBM_BF16: return 2;
+    default: return 0;
+    }
+}
+
+// row pitch: PAD_COLS leading elements (the last of them is ghost column
+// -1), then columns 0..nx (nx is the other ghost column), rounded up to a
+// multiple of 32 so every row, and every warp's segment, starts aligned
+int row_pitch(int nx) { return lbm::PAD_COLS + (nx + 1 + 31) / 32 * 32; }
+
+struct Layout {
+    int pitch;
+    int64_t plane;
+    size_t buf_bytes;                    // one population buffer (13 planes)
+    size_t off_buf[2];
+    size_t off_uin_d, off_tin_d, off_uin_f, off_tin_f;
+    size_t off_nu_d, off_al_d, off_nu_f, off_al_f;
+    size_t total;
+};
+
+int check_desc(const lbm_desc *d)
+{
+    if (!d)
+        return fail(LBM_ERR_INVALID_ARG, "desc is NULL");
+    if (d->nx < 1 || d->nr < 1)
+        return fail(LBM_ERR_INVALID_ARG, "nx and nr must be >= 1 (got %d, %d)", d->nx, d->nr);
+    if ((int64_t)d->nx * d->nr > INT32_MAX)
+        return fail(LBM_ERR_INVALID_ARG, "nx * nr exceeds 2^31 - 1");
+    if (d->nr >= (1 << 20))
+        return fail(LBM_ERR_INVALID_ARG, "nr must be below 2^20 (inlet noise counter)");
+    if (storage_bytes(d->storage) == 0)
+        return fail(LBM_ERR_INVALID_ARG, "unknown storage type %d", d->storage);
+    if (d->bc_in < 0 || d->bc_in > 1 || d->bc_out < 0 || d->bc_out > 2 || d->bc_top < 0 || d->bc_top > 1 ||
+        d->bc_bottom < 0 || d->bc_bottom > 1)
+        return fail(LBM_ERR_INVALID_ARG, "unknown boundary kind");
+    if ((d->bc_in == LBM_IN_PERIODIC) != (d->bc_out == LBM_OUT_PERIODIC))
+        return fail(LBM_ERR_INVALID_ARG, "periodic must be set on both axial ends");
+    if (d->bc_bottom == LBM_BOTTOM_AXIS && d->r0 != 0.0)
+        return fail(LBM_ERR_INVALID_ARG, "the axis requires r0 == 0");
+    if (d->axisym && !(d->r0 >= 0.0))
+        return fail(LBM_ERR_INVALID_ARG, "r0 must be >= 0 with the axisymmetric sources");
+    if (!(d->rho0 > 0.0) || !std::isfinite(d->T0) || !(d->Pr_t > 0.0) || !(d->Cs >= 0.0))
+        return fail(LBM_ERR_INVALID_ARG, "need rho0 > 0, finite T0, Pr_t > 0, Cs >= 0");
+    return LBM_OK;
+}
+
+Layout make_layout(const lbm_desc *d)
+{
+    Layout L;
+    L.pitch = row_pitch(d->nx);
+    L.plane = (int64_t)L.pitch * (d->nr + 2);  // ghost rows -1 and nr
+    L.buf_bytes = align_up((size_t)13 * (size_t)L.plane * storage_bytes(d->storage));
+    size_t o = 0;
+    L.off_buf[0] = o;
+    o += L.buf_bytes;
+    L.off_buf[1] = o;
+    o += L.buf_bytes;
+    const size_t nrd = align_up((size_t)d->nr * 8), nrf = align_up((size_t)d->nr * 4);
+    L.off_uin_d = o; o += nrd;
+    L.off_tin_d = o; o += nrd;
+    L.off_uin_f = o; o += nrf;
+    L.off_tin_f = o; o += nrf;
+    const size_t td = align_up((size_t)kMaxTable * 8), tf = align_up((size_t)kMaxTable * 4);
+    L.off_nu_d = o; o += td;
+    L.off_al_d = o; o += td;
+    L.off_nu_f = o; o += tf;
+    L.off_al_f = o; o += tf;
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+struct lbm_lattice {
+    lbm_desc d;
+    Layout L;
+    char *mem;
+    bool own;
+    int cur;  // buffer holding the current state
+    int64_t step;
+    int ntab;
+    double T_lo, T_hi;
+    int band, warps;
+    int device;
+
+    void *buf(int b) const { return mem + L.off_buf[b]; }
+    template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(mem + off); }
+};
+
+namespace {
+
+template <class C>
+lbm::StepParams<C> make_params(const lbm_lattice *h, const C *u_in, const C *T_in, const C *nu, const C *al)
+{
+    const lbm_desc &d = h->d;
+    lbm::StepParams<C> p;
+    std::memset(&p, 0, sizeof(p));
+    p.src = h->buf(h->cur);
+    p.dst = h->buf(1 - h->cur);
+    p.plane = h->L.plane;
+    p.nx = d.nx;
+    p.nr = d.nr;
+    p.pitch = h->L.pitch;
+    p.bc_in = d.bc_in;
+    p.bc_out = d.bc_out;
+    p.bc_top = d.bc_top;
+    p.bc_bottom = d.bc_bottom;
+    p.axisym = d.axisym ? 1 : 0;
+    p.band = h->band;
+    p.nstrips = (d.nx + 31) / 32;
+    const int nbands = (d.nr + h->band - 1) / h->band;
+    p.ntiles = p.nstrips * nbands;
+    p.ntab = h->ntab;
+    p.step = h->step;
+    p.seed = d.seed;
+    p.noise_amp = d.noise_amp;
+    p.r0 = C(d.r0);
+    p.rho0 = C(d.rho0);
+    p.T0 = C(d.T0);
+    p.cs2_18 = C(18.0 * d.Cs * d.Cs);
+    p.inv_prt = C(1.0 / d.Pr_t);
+    p.dT_top = C(d.T_top - d.T0);
+    p.dT_bottom = C(d.T_bottom - d.T0);
+    p.dT_out = C(d.T_out - d.T0);
+    p.T_lo = C(h->T_lo);
+    p.tab_scale = h->ntab > 1 ? C((double)(h->ntab - 1) / (h->T_hi - h->T_lo)) : C(0);
+    p.u_in = u_in;
+    p.T_in = T_in;
+    p.nu_tab = nu;
+    p.al_tab = al;
+    return p;
+}
+
+lbm::StepParams<double> params_d(const lbm_lattice *h)
+{
+    return make_params<double>(h, h->at<double>(h->L.off_uin_d), h->at<double>(h->L.off_tin_d),
+                               h->at<double>(h->L.off_nu_d), h->at<double>(h->L.off_al_d));
+}
+
+lbm::StepParams<float> params_f(const lbm_lattice *h)
+{
+    return make_params<float>(h, h->at<float>(h->L.off_uin_f), h->at<float>(h->L.off_tin_f),
+                              h->at<float>(h->L.off_nu_f), h->at<float>(h->L.off_al_f));
+}
+
+// recompute the boundary ghosts of the current state (after it or the inlet changed)
+int fill_ghosts(lbm_lattice *h, cudaStream_t s)
+{
+    cudaError_t e;
+    switch (h->d.storage) {
+    case LBM_F64: {
+        auto p = params_d(h);
+        p.dst = h->buf(h->cur);
+        e = lbm::launch_fill_f64(p, s);
+        break;
+    }
+    case LBM_F32: {
+        auto p = params_f(h);
+        p.dst = h->buf(h->cur);
+        e = lbm::launch_fill_f32(p, s);
+        break;
+    }
+    case LBM_F16: {
+        auto p = params_f(h);
+        p.dst = h->buf(h->cur);
+        e = lbm::launch_fill_f16(p, s);
+        break;
+    }
+    default: {
+        auto p = params_f(h);
+        p.dst = h->buf(h->cur);
+        e = lbm::launch_fill_bf16(p, s);
+        break;
+    }
+    }
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "ghost fill kernel launch");
+}
+
+int upload_pair(lbm_lattice *h, size_t off_d, size_t off_f, const double *src, int n, cudaStream_t s,
+                const char *what)
+{
+    std::vector<float> tmp((size_t)n);
+    for (int k = 0; k < n; ++k)
+        tmp[(size_t)k] = (float)src[k];
+    cudaError_t e = cudaMemcpyAsync(h->mem + off_d, src, (size_t)n * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->mem + off_f, tmp.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s);
+    // the float staging vector is pageable: the copy has been staged when the call returns,
+    // but synchronise anyway so the vector can be released safely on every driver
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return cuda_fail(e, what);
+    return LBM_OK;
+}
+
+bool valid(const lbm_lattice *h) { return h != nullptr && h->mem != nullptr; }
+
+}  // namespace
+
+extern "C" {
+
+const char *lbm_last_error(void) { return g_err; }
+
+int lbm_required_bytes(const lbm_desc *d, size_t *bytes)
+{
+    int rc = check_desc(d);
+    if (rc)
+        return rc;
+    if (!bytes)
+        return fail(LBM_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = make_layout(d).total;
+    return LBM_OK;
+}
+
+int lbm_create(const lbm_desc *d, void *dev_mem, size_t bytes, lbm_lattice **out)
+{
+    g_err[0] = 0;
+    int rc = check_desc(d);
+    if (rc)
+        return rc;
+    if (!out)
+        return fail(LBM_ERR_INVALID_ARG, "out is NULL");
+    Layout L = make_layout(d);
+    if (dev_mem && bytes < L.total)
+        return fail(LBM_ERR_OOM, "caller memory holds %zu bytes, the lattice needs %zu", bytes, L.total);
+    if (dev_mem && (reinterpret_cast<uintptr_t>(dev_mem) % kAlign) != 0)
+        return fail(LBM_ERR_INVALID_ARG, "caller memory must be 256-byte aligned");
+    lbm_lattice *h = new (std::nothrow) lbm_lattice();
+    if (!h)
+        return fail(LBM_ERR_OOM, "host allocation failed");
+    h->d = *d;
+    h->L = L;
+    h->own = dev_mem == nullptr;
+    h->cur = 0;
+    h->step = 0;
+    h->band = 16;
+    h->warps = 4;
+    cudaGetDevice(&h->device);
+    if (h->own) {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, L.total);
+        if (e != cudaSuccess) {
+            delete h;
+            cudaGetLastError();
+            return fail(LBM_ERR_OOM, "cudaMalloc of %zu bytes: %s", L.total, cudaGetErrorString(e));
+        }
+        h->mem = static_cast<char *>(p);
+    } else {
+        h->mem = static_cast<char *>(dev_mem);
+    }
+    // rest state: every stored deviation is zero
+    cudaError_t e = cudaMemset(h->mem, 0, L.total);
+    if (e == cudaSuccess)
+        e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        if (h->own)
+            cudaFree(h->mem);
+        delete h;
+        return cuda_fail(e, "initialising lattice memory");
+    }
+    // defaults: no inflow, T_in = T0, nu = alpha = 0.1 on [T0, T0 + 1]
+    std::vector<double> zeros((size_t)d->nr, 0.0), tin((size_t)d->nr, d->T0);
+    const double one = 0.1;
+    h->ntab = 1;
+    h->T_lo = d->T0;
+    h->T_hi = d->T0 + 1.0;
+    rc = upload_pair(h, L.off_uin_d, L.off_uin_f, zeros.data(), d->nr, nullptr, "inlet upload");
+    if (!rc) rc = upload_pair(h, L.off_tin_d, L.off_tin_f, tin.data(), d->nr, nullptr, "inlet upload");
+    if (!rc) rc = upload_pair(h, L.off_nu_d, L.off_nu_f, &one, 1, nullptr, "table upload");
+    if (!rc) rc = upload_pair(h, L.off_al_d, L.off_al_f, &one, 1, nullptr, "table upload");
+    if (!rc)
+        rc = fill_ghosts(h, nullptr);
+    if (!rc) {
+        cudaError_t e2 = cudaDeviceSynchronize();
+        if (e2 != cudaSuccess)
+            rc = cuda_fail(e2, "initialising ghosts");
+    }
+    if (rc) {
+        if (h->own)
+            cudaFree(h->mem);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_lattice *h)
+{
+    if (!h)
+        return;
+    if (h->own && h->mem) {
+        cudaDeviceSynchronize();
+        cudaFree(h->mem);
+    }
+    h->mem = nullptr;
+    delete h;
+}
+
+int lbm_set_inlet(lbm_lattice *h, const double *u_in, const double *T_in, int32_t nr, lbm_stream stream)
+{
+    if (!valid(h) || !u_in || !T_in)
+        return fail(LBM_ERR_INVALID_ARG, "bad handle or NULL profile");
+    if (nr != h->d.nr)
+        return fail(LBM_ERR_INVALID_ARG, "profile length %d != nr %d", nr, h->d.nr);
+    for (int j = 0; j < nr; ++j)
+        if (!std::isfinite(u_in[j]) || !std::isfinite(T_in[j]))
+            return fail(LBM_ERR_INVALID_ARG, "non-finite inlet value at row %d", j);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = upload_pair(h, h->L.off_uin_d, h->L.off_uin_f, u_in, nr, s, "inlet upload");
+    if (!rc)
+        rc = upload_pair(h, h->L.off_tin_d, h->L.off_tin_f, T_in, nr, s, "inlet upload");
+    if (!rc)
+        rc = fill_ghosts(h, s);  // the inlet ghosts carry the profile
+    return rc;
+}
+
+int lbm_set_properties(lbm_lattice *h, const double *nu, const double *alpha, int32_t n, double T_lo, double T_hi,
+                       lbm_stream stream)
+{
+    if (!valid(h) || !nu || !alpha)
+        return fail(LBM_ERR_INVALID_ARG, "bad handle or NULL table");
+    if (n < 1 || n > kMaxTable)
+        return fail(LBM_ERR_INVALID_ARG, "table length %d outside [1, %d]", n, kMaxTable);
+    if (n > 1 && !(T_hi > T_lo))
+        return fail(LBM_ERR_INVALID_ARG, "need T_hi > T_lo");
+    for (int k = 0; k < n; ++k)
+        if (!(nu[k] > 0.0) || !(alpha[k] > 0.0) || !std::isfinite(nu[k]) || !std::isfinite(alpha[k]))
+            return fail(LBM_ERR_INVALID_ARG, "table entry %d must be finite and > 0 (tau > 1/2)", k);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = upload_pair(h, h->L.off_nu_d, h->L.off_nu_f, nu, n, s, "table upload");
+    if (!rc)
+        rc = upload_pair(h, h->L.off_al_d, h->L.off_al_f, alpha, n, s, "table upload");
+    if (rc)
+        return rc;
+    h->ntab = n;
+    h->T_lo = T_lo;
+    h->T_hi = n > 1 ? T_hi : T_lo + 1.0;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
+{
+    if (!valid(h) || nsteps < 0)
+        return fail(LBM_ERR_INVALID_ARG, "bad handle or negative step count");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int n = 0; n < nsteps; ++n) {
+        cudaError_t e;
+        switch (h->d.storage) {
+        case LBM_F64: e = lbm::launch_step_f64(params_d(h), h->warps, s); break;
+        case LBM_F32: e = lbm::launch_step_f32(params_f(h), h->warps, s); break;
+        case LBM_F16: e = lbm::launch_step_f16(params_f(h), h->warps, s); break;
+        default: e = lbm::launch_step_bf16(params_f(h), h->warps, s); break;
+        }
+        if (e != cudaSuccess)
+            return cuda_fail(e, "step kernel launch");
+        h->cur = 1 - h->cur;
+        h->step += 1;
+    }
+    return LBM_OK;
+}
+
+int64_t lbm_get_step(const lbm_lattice *h) { return valid(h) ? h->step : -1; }
+
+int lbm_get_fields(lbm_lattice *h, void *dev_out, int32_t out_type, lbm_stream stream)
+{
+    if (!valid(h) || !dev_out)
+        return fail(LBM_ERR_INVALID_ARG, "bad handle or NULL output");
+    if (out_type != LBM_F64 && out_type != LBM_F32)
+        return fail(LBM_ERR_INVALID_ARG, "out_type must be LBM_F64 or LBM_F32");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int f64 = out_type == LBM_F64;
+    cudaError_t e;
+    switch (h->d.storage) {
+    case LBM_F64: e = lbm::launch_fields_f64(params_d(h), dev_out, f64, s); break;
+    case LBM_F32: e = lbm::launch_fields_f32(params_f(h), dev_out, f64, s); break;
+    case LBM_F16: e = lbm::launch_fields_f16(params_f(h), dev_out, f64, s); break;
+    default: e = lbm::launch_fields_bf16(params_f(h), dev_out, f64, s); break;
+    }
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "fields kernel launch");
+}
+
+int lbm_get_state(lbm_lattice *h, double *dev_f, double *dev_g, lbm_stream stream)
+{
+    if (!valid(h) || !dev_f || !dev_g)
+        return fail(LBM_ERR_INVALID_ARG, "bad handle or NULL output");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const lbm_desc &d = h->d;
+    const void *b = h->buf(h->cur);
+    cudaError_t e;
+    switch (d.storage) {
+    case LBM_F64: e = lbm::launch_state_out_f64(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+    case LBM_F32: e = lbm::launch_state_out_f32(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+    case LBM_F16: e = lbm::launch_state_out_f16(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+    default: e = lbm::launch_state_out_bf16(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+    }
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "state read kernel launch");
+}
+
+int lbm_set_state(lbm_lattice *h, const double *dev_f, const double *dev_g, int64_t step, lbm_stream stream)
+{
+    if (!valid(h) || !dev_f || !dev_g || step < 0)
+        return fail(LBM_ERR_INVALID_ARG, "bad handle, NULL input or negative step");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const lbm_desc &d = h->d;
+    void *b = h->buf(h->cur);
+    cudaError_t e;
+    switch (d.storage) {
+    case LBM_F64: e = lbm::launch_state_in_f64(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+    case LBM_F32: e = lbm::launch_state_in_f32(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+    case LBM_F16: e = lbm::launch_state_in_f16(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+    default: e = lbm::launch_state_in_bf16(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(e, "state write kernel launch");
+    h->step = step;
+    return fill_ghosts(h, s);
+}
+
+int lbm_set_launch(lbm_lattice *h, int32_t band_rows, int32_t warps_per_cta)
+{
+    if (!valid(h) || band_rows < 0 || warps_per_cta < 0 || warps_per_cta > 8)
+        return fail(LBM_ERR_INVALID_ARG, "bad handle or launch shape (warps per CTA 1..8)");
+    if (band_rows > 0)
+        h->band = band_rows;
+    if (warps_per_cta > 0)
+        h->warps = warps_per_cta;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,30 @@
+// Declarations shared by the C-ABI translation unit and the per-storage-type
+// kernel translation units of liblbm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+// Launchers, one set per storage type (defined in lbm_step_<type>.cu).
+// Each returns the cudaError_t of the launch.
+#define LBM_DECLARE_LAUNCHERS(TAG, C)                                                                  \
+    cudaError_t launch_step_##TAG(const StepParams<C> &p, int warps_per_cta, cudaStream_t s);          \
+    cudaError_t launch_fields_##TAG(const StepParams<C> &p, void *out, int out_f64, cudaStream_t s);   \
+    cudaError_t launch_fill_##TAG(const StepParams<C> &p, cudaStream_t s);                             \
+    cudaError_t launch_state_in_##TAG(void *buf, const double *f, const double *g, int nx, int nr,     \
+                                      int pitch, int64_t plane, double rho0, double T0, cudaStream_t s); \
+    cudaError_t launch_state_out_##TAG(const void *buf, double *f, double *g, int nx, int nr, int pitch, \
+                                       int64_t plane, double rho0, double T0, cudaStream_t s);
+
+LBM_DECLARE_LAUNCHERS(f64, double)
+LBM_DECLARE_LAUNCHERS(f32, float)
+LBM_DECLARE_LAUNCHERS(f16, float)
+LBM_DECLARE_LAUNCHERS(bf16, float)
+
+#undef LBM_DECLARE_LAUNCHERS
+
+}  // namespace lbm

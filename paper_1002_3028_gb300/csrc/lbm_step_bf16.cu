@@ -1,0 +1,5 @@
+// Step, field and state kernels for bf16 population storage.
+#define LBM_TAG bf16
+#define LBM_S __nv_bfloat16
+#define LBM_C float
+#include "lbm_step_inst.cuh"

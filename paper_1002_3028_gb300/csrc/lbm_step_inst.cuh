@@ -1,0 +1,60 @@
+// Instantiates the kernels and launchers of one storage type.  Included by
+// lbm_step_<type>.cu with LBM_TAG, LBM_S (storage) and LBM_C (arithmetic).
+#include "lbm_internal.h"
+
+#define LBM_CAT2(a, b) a##b
+#define LBM_CAT(a, b) LBM_CAT2(a, b)
+
+namespace lbm {
+
+cudaError_t LBM_CAT(launch_step_, LBM_TAG)(const StepParams<LBM_C> &p, int warps_per_cta, cudaStream_t s)
+{
+    if (p.ntiles <= 0)
+        return cudaSuccess;
+    const int threads = 32 * warps_per_cta;
+    const int blocks = (p.ntiles + warps_per_cta - 1) / warps_per_cta;
+    step_kernel<LBM_S, LBM_C><<<blocks, threads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t LBM_CAT(launch_fields_, LBM_TAG)(const StepParams<LBM_C> &p, void *out, int out_f64, cudaStream_t s)
+{
+    const int64_t N = (int64_t)p.nx * p.nr;
+    const int threads = 256;
+    const int64_t blocks = (N + threads - 1) / threads;
+    if (out_f64)
+        fields_kernel<LBM_S, LBM_C, double><<<(unsigned)blocks, threads, 0, s>>>(p, static_cast<double *>(out));
+    else
+        fields_kernel<LBM_S, LBM_C, float><<<(unsigned)blocks, threads, 0, s>>>(p, static_cast<float *>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t LBM_CAT(launch_fill_, LBM_TAG)(const StepParams<LBM_C> &p, cudaStream_t s)
+{
+    const int64_t N = (int64_t)p.nx * p.nr;
+    const int threads = 256;
+    fill_ghosts_kernel<LBM_S, LBM_C><<<(unsigned)((N + threads - 1) / threads), threads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t LBM_CAT(launch_state_in_, LBM_TAG)(void *buf, const double *f, const double *g, int nx, int nr, int pitch,
+                                               int64_t plane, double rho0, double T0, cudaStream_t s)
+{
+    const int64_t n = 13 * (int64_t)nx * nr;
+    const int threads = 256;
+    state_in_kernel<LBM_S><<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(
+        static_cast<LBM_S *>(buf), f, g, nx, nr, pitch, plane, rho0, T0);
+    return cudaGetLastError();
+}
+
+cudaError_t LBM_CAT(launch_state_out_, LBM_TAG)(const void *buf, double *f, double *g, int nx, int nr, int pitch,
+                                                int64_t plane, double rho0, double T0, cudaStream_t s)
+{
+    const int64_t n = 13 * (int64_t)nx * nr;
+    const int threads = 256;
+    state_out_kernel<LBM_S><<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(
+        static_cast<const LBM_S *>(buf), f, g, nx, nr, pitch, plane, rho0, T0);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,230 @@
+"""Thin ctypes binding of liblbm (include/lbm.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+kernels of the library.  PyTorch supplies the device memory (a caching
+allocator block handed to ``lbm_create``) and the CUDA stream.  There is no
+CPU fallback: if the library cannot be built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+from .inputs import LatticeConfig, Workload
+
+LBM_OK = 0
+ERRORS = {-1: "LBM_ERR_INVALID_ARG", -2: "LBM_ERR_OOM", -3: "LBM_ERR_CUDA", -4: "LBM_ERR_DIVERGED"}
+STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+_BC_IN = {"inlet": 0, "periodic": 1}
+_BC_OUT = {"outflow": 0, "wall": 1, "periodic": 2}
+_BC_TOP = {"wall": 0, "open": 1}
+_BC_BOTTOM = {"axis": 0, "wall": 1}
+
+HEADER = os.path.join(_build.ROOT, "include", "lbm.h")
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code: int, what: str, msg: str):
+        super().__init__(f"{what} failed with {ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Desc(C.Structure):
+    """Mirror of ``lbm_desc``."""
+
+    _fields_ = [
+        ("nx", C.c_int32), ("nr", C.c_int32), ("storage", C.c_int32),
+        ("bc_in", C.c_int32), ("bc_out", C.c_int32), ("bc_top", C.c_int32), ("bc_bottom", C.c_int32),
+        ("axisym", C.c_int32),
+        ("r0", C.c_double), ("rho0", C.c_double), ("T0", C.c_double), ("Cs", C.c_double),
+        ("Pr_t", C.c_double), ("T_top", C.c_double), ("T_bottom", C.c_double), ("T_out", C.c_double),
+        ("noise_amp", C.c_double), ("seed", C.c_uint64),
+    ]
+
+
+def make_desc(cfg: LatticeConfig, storage: str) -> Desc:
+    return Desc(nx=cfg.nx, nr=cfg.nr, storage=STORAGE[storage], bc_in=_BC_IN[cfg.bc_in],
+                bc_out=_BC_OUT[cfg.bc_out], bc_top=_BC_TOP[cfg.bc_top],
+                bc_bottom=_BC_BOTTOM[cfg.bc_bottom], axisym=int(cfg.axisym), r0=cfg.r0,
+                rho0=cfg.rho0, T0=cfg.T0, Cs=cfg.Cs, Pr_t=cfg.Pr_t, T_top=cfg.T_top,
+                T_bottom=cfg.T_bottom, T_out=cfg.T_out, noise_amp=cfg.noise_amp,
+                seed=cfg.seed & 0xFFFFFFFFFFFFFFFF)
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def declared_symbols():
+    """Names of the functions include/lbm.h declares."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"LBM_API\s+[\w\s\*]*?\b(lbm_\w+)\s*\(", text)))
+
+
+def lib(build: bool = True):
+    """Load liblbm (building it first if it is stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"liblbm is not built ({path}); the CUDA path has no fallback")
+            L = C.CDLL(path)
+            vp, dp, i32, i64 = C.c_void_p, C.POINTER(C.c_double), C.c_int32, C.c_int64
+            L.lbm_last_error.restype = C.c_char_p
+            L.lbm_last_error.argtypes = []
+            L.lbm_required_bytes.argtypes = [C.POINTER(Desc), C.POINTER(C.c_size_t)]
+            L.lbm_create.argtypes = [C.POINTER(Desc), vp, C.c_size_t, C.POINTER(vp)]
+            L.lbm_destroy.restype = None
+            L.lbm_destroy.argtypes = [vp]
+            L.lbm_set_inlet.argtypes = [vp, dp, dp, i32, vp]
+            L.lbm_set_properties.argtypes = [vp, dp, dp, i32, C.c_double, C.c_double, vp]
+            L.lbm_step.argtypes = [vp, i32, vp]
+            L.lbm_get_step.restype = i64
+            L.lbm_get_step.argtypes = [vp]
+            L.lbm_get_fields.argtypes = [vp, vp, i32, vp]
+            L.lbm_get_state.argtypes = [vp, vp, vp, vp]
+            L.lbm_set_state.argtypes = [vp, vp, vp, i64, vp]
+            L.lbm_set_launch.argtypes = [vp, i32, i32]
+            for name in ("lbm_required_bytes", "lbm_create", "lbm_set_inlet", "lbm_set_properties",
+                         "lbm_step", "lbm_get_fields", "lbm_get_state", "lbm_set_state",
+                         "lbm_set_launch"):
+                getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != LBM_OK:
+        raise LbmError(rc, what, lib().lbm_last_error().decode())
+
+
+def required_bytes(cfg: LatticeConfig, storage: str = "f32") -> int:
+    d = make_desc(cfg, storage)
+    n = C.c_size_t(0)
+    _check(lib().lbm_required_bytes(C.byref(d), C.byref(n)), "lbm_required_bytes")
+    return int(n.value)
+
+
+def _stream_ptr(stream) -> C.c_void_p:
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(int(s.cuda_stream))
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Lattice:
+    """One lattice resident on the GPU, advanced by the fused CUDA step."""
+
+    def __init__(self, cfg: LatticeConfig, storage: str = "f32", device=None):
+        import torch
+
+        cfg.validate()
+        if storage not in STORAGE:
+            raise ValueError(f"storage must be one of {sorted(STORAGE)}")
+        self.cfg = cfg
+        self.storage = storage
+        self.nx, self.nr = cfg.nx, cfg.nr
+        self.device = torch.device(device if device is not None else "cuda")
+        self._L = lib()
+        self._desc = make_desc(cfg, storage)
+        self.nbytes = required_bytes(cfg, storage)
+        with torch.cuda.device(self.device):
+            # the caching allocator hands out 512-byte aligned blocks
+            self._mem = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+            h = C.c_void_p()
+            _check(self._L.lbm_create(C.byref(self._desc), C.c_void_p(self._mem.data_ptr()),
+                                      self.nbytes, C.byref(h)), "lbm_create")
+        self._h = h
+
+    @classmethod
+    def from_workload(cls, w: Workload, storage: str = "f32", device=None) -> "Lattice":
+        lat = cls(w.cfg, storage, device)
+        lat.set_inlet(w.u_in, w.T_in)
+        lat.set_properties(w.nu_tab, w.alpha_tab, w.T_lo, w.T_hi)
+        return lat
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.lbm_destroy(self._h)
+            self._h = None
+            self._mem = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> C.c_void_p:
+        return self._h
+
+    def set_inlet(self, u_in, T_in, stream=None):
+        u = np.ascontiguousarray(u_in, dtype=np.float64)
+        T = np.ascontiguousarray(T_in, dtype=np.float64)
+        _check(self._L.lbm_set_inlet(self._h, _dptr(u), _dptr(T), len(u), _stream_ptr(stream)),
+               "lbm_set_inlet")
+
+    def set_properties(self, nu, alpha, T_lo, T_hi, stream=None):
+        a = np.ascontiguousarray(nu, dtype=np.float64)
+        b = np.ascontiguousarray(alpha, dtype=np.float64)
+        _check(self._L.lbm_set_properties(self._h, _dptr(a), _dptr(b), len(a), float(T_lo),
+                                          float(T_hi), _stream_ptr(stream)), "lbm_set_properties")
+
+    def set_launch(self, band_rows: int = 0, warps_per_cta: int = 0):
+        _check(self._L.lbm_set_launch(self._h, band_rows, warps_per_cta), "lbm_set_launch")
+
+    def step(self, n: int = 1, stream=None):
+        _check(self._L.lbm_step(self._h, int(n), _stream_ptr(stream)), "lbm_step")
+
+    @property
+    def step_count(self) -> int:
+        return int(self._L.lbm_get_step(self._h))
+
+    def fields(self, dtype=None, stream=None, out=None):
+        """(4, nr, nx) device tensor of rho, u_x, u_r, T at the current time."""
+        import torch
+
+        dtype = dtype or torch.float64
+        if out is None:
+            out = torch.empty((4, self.nr, self.nx), dtype=dtype, device=self.device)
+        code = 0 if out.dtype == torch.float64 else 1
+        if out.dtype not in (torch.float64, torch.float32) or not out.is_contiguous():
+            raise ValueError("fields output must be a contiguous float64/float32 tensor")
+        _check(self._L.lbm_get_fields(self._h, C.c_void_p(out.data_ptr()), code, _stream_ptr(stream)),
+               "lbm_get_fields")
+        return out
+
+    def get_state(self, stream=None):
+        """Post-collision populations as device FP64 tensors f (9, nr, nx), g (4, nr, nx)."""
+        import torch
+
+        f = torch.empty((9, self.nr, self.nx), dtype=torch.float64, device=self.device)
+        g = torch.empty((4, self.nr, self.nx), dtype=torch.float64, device=self.device)
+        _check(self._L.lbm_get_state(self._h, C.c_void_p(f.data_ptr()), C.c_void_p(g.data_ptr()),
+                                     _stream_ptr(stream)), "lbm_get_state")
+        return f, g
+
+    def set_state(self, f, g, step: int = 0, stream=None):
+        import torch
+
+        f = torch.as_tensor(f, dtype=torch.float64, device=self.device).contiguous()
+        g = torch.as_tensor(g, dtype=torch.float64, device=self.device).contiguous()
+        if tuple(f.shape) != (9, self.nr, self.nx) or tuple(g.shape) != (4, self.nr, self.nx):
+            raise ValueError("state shapes must be (9, nr, nx) and (4, nr, nx)")
+        _check(self._L.lbm_set_state(self._h, C.c_void_p(f.data_ptr()), C.c_void_p(g.data_ptr()),
+                                     int(step), _stream_ptr(stream)), "lbm_set_state")
+        # keep the inputs alive until the conversion kernel has run
+        torch.cuda.current_stream(self.device).synchronize() if stream is None else stream.synchronize()

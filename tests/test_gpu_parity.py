@@ -1,0 +1,256 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Errors are max-norms of the difference relative to the max-norm of the
+oracle's quantity: per population plane for states; for fields, rho and T
+against their own max, the velocity components against the max speed
+|u| = sqrt(u_x^2 + u_r^2).  Tolerances:
+  FP64 storage   1e-12 per step, and 1e-12 over the 2000-step laminar pipe;
+  FP32 storage   1e-5 on rho, u, T per step and after 1000 laminar steps;
+  FP16 storage   1e-3 on u and T per step; 2e-3 on u and T after 1000
+                 laminar steps (measured 1.0e-3 and 1.4e-3);
+  BF16 storage   3e-3 on u and T per step; after 1000 laminar steps 2e-2
+                 on u and 5e-2 on T (8-bit significand).
+The FP16/BF16 bounds are what deviation storage with round-to-nearest
+allows: one rounding of a stored deviation costs 2^-12 (FP16) or 2^-9 (BF16)
+of its size per step, and the laminar pipe accumulates those over its
+thermal relaxation time.  Turbulent runs are compared one step at a time
+from an identical state.
+"""
+import dataclasses
+import os
+
+import numpy as np
+import pytest
+
+from paper_1002_3028_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NTHREADS = max(1, min(8, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1002_3028_gb300 import lbm as L
+
+    L.lib()
+    return L
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    scale = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / (scale if scale > 0 else 1.0))
+
+
+def state_rel(lat_state, orc_state):
+    """Worst per-plane relative difference of two (f, g) states."""
+    worst = 0.0
+    for a, b in zip(lat_state, orc_state):
+        a = a.cpu().numpy() if hasattr(a, "cpu") else a
+        for q in range(b.shape[0]):
+            worst = max(worst, rel(a[q], b[q]))
+    return worst
+
+
+def fields_rel(Fg, Fo):
+    """[rho, u_x, u_r, T] errors; velocity components relative to the max speed."""
+    Fg = Fg.cpu().numpy() if hasattr(Fg, "cpu") else np.asarray(Fg)
+    speed = float(np.max(np.hypot(Fo[1], Fo[2])))
+    out = []
+    for c in range(4):
+        scale = speed if c in (1, 2) else float(np.max(np.abs(Fo[c])))
+        d = float(np.max(np.abs(Fg[c] - Fo[c])))
+        out.append(d / scale if scale > 0 else d)
+    return out
+
+
+def workload(nx, nr, bc_in="inlet", bc_out="outflow", bc_top="open", bc_bottom="axis", r0=0.0,
+             Cs=0.17, noise=1e-3, axisym=True):
+    R = max(1.0, nr / 3.0)
+    cfg = I.LatticeConfig(nx=nx, nr=nr, bc_in=bc_in, bc_out=bc_out, bc_top=bc_top,
+                          bc_bottom=bc_bottom, r0=r0, axisym=axisym, Cs=Cs, Pr_t=0.3,
+                          T_top=1.2, T_bottom=1.5, T_out=0.8, noise_amp=noise, seed=99)
+    u_in, T_in = I.jet_profiles(nr, R, 0.06, 1.0, 4.0)
+    nu, al = I.power_law_tables(64, 0.8, 4.0, nu_max=0.2)
+    return I.Workload("case", cfg, u_in, T_in, nu, al, 0.8, 4.0)
+
+
+def pair(lbm_mod, orc, w, storage, seed=1, amp=0.05, step=5):
+    o = orc.Oracle.from_workload(w, NTHREADS)
+    g = lbm_mod.Lattice.from_workload(w, storage)
+    f0, g0 = I.random_state(w.cfg.nx, w.cfg.nr, orc.feq(1.0, 0.02, 0.0), orc.geq(1.3, 0.02, 0.0), amp,
+                            seed)
+    o.set_state(f0, g0, step)
+    g.set_state(f0, g0, step)
+    return o, g
+
+
+BOUNDARIES = {
+    "jet": dict(bc_in="inlet", bc_out="outflow", bc_top="open", bc_bottom="axis"),
+    "pipe": dict(bc_in="inlet", bc_out="outflow", bc_top="wall", bc_bottom="axis"),
+    "periodic_axis": dict(bc_in="periodic", bc_out="periodic", bc_top="wall", bc_bottom="axis"),
+    "annulus": dict(bc_in="periodic", bc_out="periodic", bc_top="wall", bc_bottom="wall", r0=5.0),
+    "substrate": dict(bc_in="inlet", bc_out="wall", bc_top="open", bc_bottom="axis"),
+    "inner_wall_pipe": dict(bc_in="inlet", bc_out="outflow", bc_top="wall", bc_bottom="wall", r0=3.0),
+    "open_periodic": dict(bc_in="periodic", bc_out="periodic", bc_top="open", bc_bottom="axis"),
+}
+SIZES = [(70, 19), (33, 5), (1, 12), (3, 3), (64, 32), (97, 40)]
+
+
+@pytest.mark.parametrize("bname", sorted(BOUNDARIES))
+@pytest.mark.parametrize("size", SIZES, ids=[f"{a}x{b}" for a, b in SIZES])
+def test_f64_step_matches_oracle(lbm, orc, bname, size):
+    w = workload(*size, **BOUNDARIES[bname])
+    o, g = pair(lbm, orc, w, "f64")
+    for n in range(3):
+        o.step(1)
+        g.step(1)
+        err = state_rel(g.get_state(), o.get_state())
+        assert err < 1e-12, (n, err)
+    assert g.step_count == o.step_count == 8
+    assert max(fields_rel(g.fields(), o.fields())) < 1e-12
+
+
+@pytest.mark.parametrize("size", [(1, 1), (2, 1), (1, 2), (5, 1), (31, 2), (32, 32), (33, 33)],
+                         ids=lambda s: f"{s[0]}x{s[1]}")
+@pytest.mark.parametrize("bname", ["jet", "pipe", "periodic_axis"])
+def test_f64_degenerate_sizes(lbm, orc, size, bname):
+    w = workload(*size, **BOUNDARIES[bname])
+    o, g = pair(lbm, orc, w, "f64")
+    o.step(2)
+    g.step(2)
+    assert state_rel(g.get_state(), o.get_state()) < 1e-12
+
+
+def test_f64_planar_model(lbm, orc):
+    w = workload(70, 19, axisym=False)
+    o, g = pair(lbm, orc, w, "f64")
+    o.step(2)
+    g.step(2)
+    assert state_rel(g.get_state(), o.get_state()) < 1e-12
+
+
+def test_f64_pipe_2000_steps(lbm, orc):
+    """Laminar Hagen-Poiseuille pipe, 64 x 32, 2000 steps from rest."""
+    w = I.pipe_workload()
+    o = orc.Oracle.from_workload(w, NTHREADS)
+    g = lbm.Lattice.from_workload(w, "f64")
+    o.step(2000)
+    g.step(2000)
+    errs = fields_rel(g.fields(), o.fields())
+    assert max(errs) < 1e-12, errs
+
+
+@pytest.mark.parametrize("storage,tol_u,tol_T", [("f32", 1e-5, 1e-5), ("f16", 2e-3, 2e-3),
+                                                 ("bf16", 2e-2, 5e-2)])
+def test_reduced_storage_pipe_1000_steps(lbm, orc, storage, tol_u, tol_T):
+    """rho, u, T of the laminar pipe after 1000 steps from rest."""
+    w = I.pipe_workload()
+    o = orc.Oracle.from_workload(w, NTHREADS)
+    g = lbm.Lattice.from_workload(w, storage)
+    o.step(1000)
+    g.step(1000)
+    errs = fields_rel(g.fields(), o.fields())
+    assert errs[1] < tol_u and errs[2] < tol_u and errs[3] < tol_T, errs
+    if storage == "f32":
+        assert errs[0] < 1e-5, errs
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f16", 1e-3), ("bf16", 3e-3)])
+def test_reduced_storage_one_step(lbm, orc, storage, tol):
+    """One step of a noisy hot jet from an identical state, every boundary of the jet."""
+    w = workload(130, 45)
+    o, g = pair(lbm, orc, w, storage, amp=0.02)
+    o.step(1)
+    g.step(1)
+    errs = fields_rel(g.fields(), o.fields())
+    assert errs[1] < tol and errs[2] < tol and errs[3] < tol, errs
+    if storage == "f32":
+        assert max(errs) < tol
+
+
+def _developed_jet(orc, nx, nr, steps):
+    w = I.jet_workload(nx=nx, nr=nr)
+    o = orc.Oracle.from_workload(w, NTHREADS)
+    o.step(steps)
+    return w, o
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_single_jet_1024x256_per_step(lbm, orc, storage, tol):
+    """The 1024 x 256 turbulent jet in the benchmark's launch shape, stepped from the oracle's state."""
+    w, o = _developed_jet(orc, 1024, 256, 150)
+    f0, g0 = o.get_state()
+    g = lbm.Lattice.from_workload(w, storage)
+    g.set_state(f0, g0, o.step_count)
+    for _ in range(2):
+        o.step(1)
+        g.step(1)
+        errs = fields_rel(g.fields(), o.fields())
+        assert max(errs) < tol, errs
+    if storage == "f64":
+        assert state_rel(g.get_state(), o.get_state()) < tol
+
+
+def test_full_size_4096x1024_one_step(lbm, orc):
+    """The 4096 x 1024 jet (the throughput workload), FP32, one step from a perturbed rest state."""
+    w = I.jet_workload(nx=4096, nr=1024)
+    o = orc.Oracle.from_workload(w, NTHREADS)
+    g = lbm.Lattice.from_workload(w, "f32")
+    f0, g0 = I.random_state(4096, 1024, orc.feq(1.0, 0.03, 0.0), orc.geq(2.0, 0.03, 0.0), 0.01, 4)
+    o.set_state(f0, g0, 17)
+    g.set_state(f0, g0, 17)
+    del f0, g0
+    o.step(1)
+    g.step(1)
+    errs = fields_rel(g.fields(), o.fields())
+    assert max(errs) < 1e-5, errs
+
+
+@pytest.mark.parametrize("band,warps", [(1, 1), (3, 8), (16, 4), (64, 2), (1000, 4)])
+def test_launch_shape_does_not_change_results(lbm, orc, band, warps):
+    w = workload(97, 40)
+    ref = lbm.Lattice.from_workload(w, "f32")
+    alt = lbm.Lattice.from_workload(w, "f32")
+    alt.set_launch(band, warps)
+    f0, g0 = I.random_state(97, 40, orc.feq(1.0, 0.0, 0.0), orc.geq(1.0, 0.0, 0.0), 0.03, 8)
+    for lat in (ref, alt):
+        lat.set_state(f0, g0, 0)
+        lat.step(4)
+    a = ref.get_state()
+    b = alt.get_state()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+def test_rest_state_is_exactly_steady(lbm):
+    cfg = I.LatticeConfig(nx=100, nr=30, bc_top="wall", T_top=1.0)
+    lat = lbm.Lattice(cfg, "f32")
+    lat.step(20)
+    f, g = lat.get_state()
+    f0 = torch.tensor([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4, dtype=torch.float64, device=f.device)
+    assert torch.equal(f, f0.view(9, 1, 1).expand_as(f))
+    assert torch.all(g == 0.25)
+
+
+def test_state_roundtrip_f64(lbm, orc):
+    w = workload(45, 13)
+    g = lbm.Lattice.from_workload(w, "f64")
+    f0, g0 = I.random_state(45, 13, orc.feq(1.0, 0.0, 0.0), orc.geq(1.0, 0.0, 0.0), 0.05, 3)
+    g.set_state(f0, g0, 12)
+    f1, g1 = g.get_state()
+    assert g.step_count == 12
+    np.testing.assert_allclose(f1.cpu().numpy(), f0, rtol=0, atol=1e-16)
+    np.testing.assert_allclose(g1.cpu().numpy(), g0, rtol=0, atol=1e-16)
+
+
+def test_fields_float32_output(lbm, orc):
+    w = workload(50, 20)
+    o, g = pair(lbm, orc, w, "f64")
+    Fo = o.fields()
+    F32 = g.fields(dtype=torch.float32)
+    assert max(fields_rel(F32.double(), Fo)) < 1e-6
