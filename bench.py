@@ -194,7 +194,7 @@ def run_gpu(args):
     w = workload_by_name(args.workload)
     lat = lbm.Lattice.from_workload(w, args.storage, device=device)
     if args.band or args.warps:
-        lat.set_launch(args.band, args.warps)
+        lat.set_launch(max(args.band, 0), args.warps)
     stream = torch.cuda.current_stream(device)
 
     def barrier():
@@ -279,7 +279,8 @@ def run_gpu(args):
                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2": "no flush: inputs larger than L2 (two population buffers of "
                          f"{2 * POPS * BYTES_PER_VALUE[args.storage] * nodes / 1e6:.0f} MB)",
-                   "bytes_per_lup": bpl},
+                   "bytes_per_lup": bpl,
+                   "launch": dict(zip(("band_rows", "warps_per_cta", "ctas"), lat.launch()))},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic},
         "cpu_baseline": cpu,
@@ -298,7 +299,7 @@ def run_gpu(args):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="jet4096x1024")

@@ -178,11 +178,17 @@ LBM_API int lbm_set_state(lbm_lattice *h, const double *dev_f, const double *dev
                   lbm_stream stream);
 
 /*
- * Launch shape of the step kernel: rows per warp tile (band height, >= 1)
- * and warps per CTA (1..8).  0 keeps the current value.  Used by the
- * autotuner; results do not depend on it.
+ * Launch shape of the step kernel: CTAs of warps_per_cta warps (1..8), one
+ * warp per tile of 32 columns x band_rows rows.  band_rows >= 1 fixes the
+ * band height; 0 lets the library choose it from the number of warps the GPU
+ * holds at once (the default).  warps_per_cta == 0 keeps the current value.
+ * Results do not depend on the launch shape.
  */
 LBM_API int lbm_set_launch(lbm_lattice *h, int32_t band_rows, int32_t warps_per_cta);
+
+/* The launch shape lbm_step uses: band height, warps per CTA and CTAs per
+ * launch (any pointer may be NULL). */
+LBM_API int lbm_get_launch(const lbm_lattice *h, int32_t *band_rows, int32_t *warps_per_cta, int32_t *ctas);
 
 #ifdef __cplusplus
 }

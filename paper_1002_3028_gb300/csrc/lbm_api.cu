@@ -48,9 +48,11 @@ size_t storage_bytes(int storage)
 }
 
 // row pitch: PAD_COLS leading elements (the last of them is ghost column
-// -1), then columns 0..nx (nx is the other ghost column), rounded up to a
-// multiple of 32 so every row, and every warp's segment, starts aligned
-int row_pitch(int nx) { return lbm::PAD_COLS + (nx + 1 + 31) / 32 * 32; }
+// -1), then columns 0..nx (nx is the other ghost column) rounded up to a
+// multiple of 32, then 32 more so a warp's staged window (its 32 columns and
+// a 16-byte halo on each side) never leaves the row; every row and every
+// warp segment starts on a 64-byte boundary
+int row_pitch(int nx) { return lbm::PAD_COLS + (nx + 1 + 31) / 32 * 32 + 32; }
 
 struct Layout {
     int pitch;
@@ -124,8 +126,9 @@ struct lbm_lattice {
     int64_t step;
     int ntab;
     double T_lo, T_hi;
-    int band, warps;
-    int device;
+    int band, warps;       // launch shape; band 0 = chosen from the occupancy
+    int band_eff, ctas;    // band and CTA count used by lbm_step
+    int device, sms;
 
     void *buf(int b) const { return mem + L.off_buf[b]; }
     template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(mem + off); }
@@ -150,9 +153,9 @@ lbm::StepParams<C> make_params(const lbm_lattice *h, const C *u_in, const C *T_i
     p.bc_top = d.bc_top;
     p.bc_bottom = d.bc_bottom;
     p.axisym = d.axisym ? 1 : 0;
-    p.band = h->band;
+    p.band = h->band_eff;
     p.nstrips = (d.nx + 31) / 32;
-    const int nbands = (d.nr + h->band - 1) / h->band;
+    const int nbands = (d.nr + h->band_eff - 1) / h->band_eff;
     p.ntiles = p.nstrips * nbands;
     p.ntab = h->ntab;
     p.step = h->step;
@@ -185,6 +188,39 @@ lbm::StepParams<float> params_f(const lbm_lattice *h)
 {
     return make_params<float>(h, h->at<float>(h->L.off_uin_f), h->at<float>(h->L.off_tin_f),
                               h->at<float>(h->L.off_nu_f), h->at<float>(h->L.off_al_f));
+}
+
+// Launch shape of the step kernel: one warp per 32-column x band-row tile,
+// all tiles in one grid.  The automatic band height keeps about four tiles
+// per resident warp (so CTAs start and finish at staggered times and the
+// last wave is short), bounded to 4..32 rows (each band pulls two extra
+// halo rows).
+int plan_launch(lbm_lattice *h)
+{
+    int per_sm = 0;
+    cudaError_t e;
+    switch (h->d.storage) {
+    case LBM_F64: e = lbm::occupancy_step_f64(h->warps, &per_sm); break;
+    case LBM_F32: e = lbm::occupancy_step_f32(h->warps, &per_sm); break;
+    case LBM_F16: e = lbm::occupancy_step_f16(h->warps, &per_sm); break;
+    default: e = lbm::occupancy_step_bf16(h->warps, &per_sm); break;
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(e, "occupancy query");
+    if (per_sm < 1)
+        return fail(LBM_ERR_INVALID_ARG, "a CTA of %d warps does not fit on an SM", h->warps);
+    const int resident_warps = per_sm * std::max(1, h->sms) * h->warps;
+    const int nstrips = (h->d.nx + 31) / 32;
+    if (h->band > 0) {
+        h->band_eff = h->band;
+    } else {
+        const int64_t want_tiles = 4 * (int64_t)resident_warps;
+        const int64_t band = ((int64_t)h->d.nr * nstrips + want_tiles - 1) / want_tiles;
+        h->band_eff = (int)std::min<int64_t>(32, std::max<int64_t>(4, band));
+    }
+    const int64_t ntiles = (int64_t)nstrips * ((h->d.nr + h->band_eff - 1) / h->band_eff);
+    h->ctas = (int)((ntiles + h->warps - 1) / h->warps);
+    return LBM_OK;
 }
 
 // recompute the boundary ghosts of the current state (after it or the inlet changed)
@@ -278,9 +314,11 @@ int lbm_create(const lbm_desc *d, void *dev_mem, size_t bytes, lbm_lattice **out
     h->own = dev_mem == nullptr;
     h->cur = 0;
     h->step = 0;
-    h->band = 16;
+    h->band = 0;
     h->warps = 4;
     cudaGetDevice(&h->device);
+    h->sms = 1;
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
     if (h->own) {
         void *p = nullptr;
         cudaError_t e = cudaMalloc(&p, L.total);
@@ -313,6 +351,8 @@ int lbm_create(const lbm_desc *d, void *dev_mem, size_t bytes, lbm_lattice **out
     if (!rc) rc = upload_pair(h, L.off_tin_d, L.off_tin_f, tin.data(), d->nr, nullptr, "inlet upload");
     if (!rc) rc = upload_pair(h, L.off_nu_d, L.off_nu_f, &one, 1, nullptr, "table upload");
     if (!rc) rc = upload_pair(h, L.off_al_d, L.off_al_f, &one, 1, nullptr, "table upload");
+    if (!rc)
+        rc = plan_launch(h);
     if (!rc)
         rc = fill_ghosts(h, nullptr);
     if (!rc) {
@@ -392,10 +432,10 @@ int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
     for (int n = 0; n < nsteps; ++n) {
         cudaError_t e;
         switch (h->d.storage) {
-        case LBM_F64: e = lbm::launch_step_f64(params_d(h), h->warps, s); break;
-        case LBM_F32: e = lbm::launch_step_f32(params_f(h), h->warps, s); break;
-        case LBM_F16: e = lbm::launch_step_f16(params_f(h), h->warps, s); break;
-        default: e = lbm::launch_step_bf16(params_f(h), h->warps, s); break;
+        case LBM_F64: e = lbm::launch_step_f64(params_d(h), h->warps, h->ctas, s); break;
+        case LBM_F32: e = lbm::launch_step_f32(params_f(h), h->warps, h->ctas, s); break;
+        case LBM_F16: e = lbm::launch_step_f16(params_f(h), h->warps, h->ctas, s); break;
+        default: e = lbm::launch_step_bf16(params_f(h), h->warps, h->ctas, s); break;
         }
         if (e != cudaSuccess)
             return cuda_fail(e, "step kernel launch");
@@ -466,10 +506,22 @@ int lbm_set_launch(lbm_lattice *h, int32_t band_rows, int32_t warps_per_cta)
 {
     if (!valid(h) || band_rows < 0 || warps_per_cta < 0 || warps_per_cta > 8)
         return fail(LBM_ERR_INVALID_ARG, "bad handle or launch shape (warps per CTA 1..8)");
-    if (band_rows > 0)
-        h->band = band_rows;
+    h->band = band_rows;
     if (warps_per_cta > 0)
         h->warps = warps_per_cta;
+    return plan_launch(h);
+}
+
+int lbm_get_launch(const lbm_lattice *h, int32_t *band_rows, int32_t *warps_per_cta, int32_t *ctas)
+{
+    if (!valid(h))
+        return fail(LBM_ERR_INVALID_ARG, "bad handle");
+    if (band_rows)
+        *band_rows = h->band_eff;
+    if (warps_per_cta)
+        *warps_per_cta = h->warps;
+    if (ctas)
+        *ctas = h->ctas;
     return LBM_OK;
 }
 

@@ -22,12 +22,13 @@
 // one, exactly as in the rules' definition.
 //
 // Work split of the step kernel.  One warp owns a strip of 32 consecutive
-// columns and marches up a band of rows.  For each row it pulls the 13
-// populations (one coalesced load per population), forms the Eq. 2 moments
-// and collides the row below, whose radial neighbours' moments (same time
-// level) it already holds; the axial neighbours' rho u_r comes from the
-// adjacent lanes by warp shuffle and, for the two columns beside the strip,
-// from six loads in lanes 0 and 31.
+// columns and marches up a band of rows.  The populations each row pulls are
+// staged in the warp's shared-memory ring by asynchronous copies issued two
+// rows ahead; from a landed row the warp forms the Eq. 2 moments and
+// collides the row below, whose radial neighbours' moments (same time level)
+// it already holds.  The axial neighbours' rho u_r comes from the adjacent
+// lanes by warp shuffle and, for the two columns beside the strip, from the
+// staged window's halo.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -83,6 +84,12 @@ template <> __device__ __forceinline__ double load_as<double, double>(const doub
 template <> __device__ __forceinline__ float load_as<float, float>(const float *p) { return __ldg(p); }
 template <> __device__ __forceinline__ float load_as<__half, float>(const __half *p) { return __half2float(__ldg(p)); }
 template <> __device__ __forceinline__ float load_as<__nv_bfloat16, float>(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+
+template <class S, class C> __device__ __forceinline__ C load_as_shared(const S *p);
+template <> __device__ __forceinline__ double load_as_shared<double, double>(const double *p) { return *p; }
+template <> __device__ __forceinline__ float load_as_shared<float, float>(const float *p) { return *p; }
+template <> __device__ __forceinline__ float load_as_shared<__half, float>(const __half *p) { return __half2float(*p); }
+template <> __device__ __forceinline__ float load_as_shared<__nv_bfloat16, float>(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
 
 template <class S, class C> __device__ __forceinline__ S store_as(C v);
 template <> __device__ __forceinline__ double store_as<double, double>(double v) { return v; }
@@ -449,95 +456,208 @@ __device__ __forceinline__ C jr_beyond_outlet(const StepParams<C> &p, const S *s
     return jr_at<S, C>(p, src, 0, j);
 }
 
-// ---- the fused step kernel ------------------------------------------------------------
-template <class S, class C>
-__global__ void __launch_bounds__(256) step_kernel(const __grid_constant__ StepParams<C> p)
+// ---- shared-memory staging of pulled rows -------------------------------------------
+// Each warp owns a ring of NSTAGE stages.  A stage holds, for one lattice row
+// r and each plane q, the window of source row r - e_qy over source columns
+// x0 - H .. x0 + 31 + H (H = one 16-byte chunk of elements), copied with
+// asynchronous 16-byte copies spread over the warp's lanes.  Lane l then
+// reads population q of node (x0 + l, r) at window index l + H - e_qx.
+constexpr int NSTAGE = 4;
+
+template <class S>
+struct Win {
+    static constexpr int E = 16 / (int)sizeof(S);  // elements per 16-byte chunk
+    static constexpr int H = E;                    // halo elements on each side
+    static constexpr int W = 32 + 2 * H;           // window length
+    static constexpr int CH = W / E;               // chunks per plane
+    static constexpr int STAGE = 13 * W;           // elements per stage
+};
+
+// e_y of plane q (9 D2Q9 planes, then 4 D2Q4 planes)
+__device__ __forceinline__ int plane_ey(int q)
 {
-    const int lane = threadIdx.x & 31;
-    const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (tile >= p.ntiles)
-        return;  // whole warp
+    // (e_y + 1) packed two bits per plane
+    constexpr unsigned packed = (1u << 0) | (1u << 2) | (2u << 4) | (1u << 6) | (0u << 8) | (2u << 10) | (2u << 12) |
+                                (0u << 14) | (0u << 16) | (1u << 18) | (2u << 20) | (1u << 22) | (0u << 24);
+    return (int)((packed >> (2 * q)) & 3u) - 1;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// start the copies of lattice row r into one stage
+template <class S, class C>
+__device__ __forceinline__ void issue_row(const StepParams<C> &p, const S *src, S *stage, int x0, int r, int lane)
+{
+    using Wn = Win<S>;
+    constexpr int total = 13 * Wn::CH;
+#pragma unroll
+    for (int m = 0; m < (total + 31) / 32; ++m) {
+        const int t = lane + 32 * m;
+        if (t < total) {
+            const int q = t / Wn::CH;
+            const int c = t - q * Wn::CH;
+            cp_async16(stage + q * Wn::W + c * Wn::E, src + cell(p, q, x0 - Wn::H + c * Wn::E, r - plane_ey(q)));
+        }
+    }
+}
+
+// population q of lane `col` (0..31, or -1 / 32 for the columns beside the strip)
+template <class S, class C>
+__device__ __forceinline__ C sget(const S *stage, int q, int ex, int col)
+{
+    using Wn = Win<S>;
+    return load_as_shared<S, C>(stage + q * Wn::W + col + Wn::H - ex);
+}
+
+template <class S, class C>
+__device__ __forceinline__ void stage_pops(const S *stage, int lane, C (&f)[9], C (&g)[4])
+{
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+        f[k] = sget<S, C>(stage, k, ex9(k), lane);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        g[k] = sget<S, C>(stage, 9 + k, ex4(k), lane);
+}
+
+// rho u_r of the streamed populations in window column col of a stage
+template <class S, class C>
+__device__ __forceinline__ C stage_jr(const S *stage, int col)
+{
+    return (sget<S, C>(stage, 2, 0, col) - sget<S, C>(stage, 4, 0, col)) +
+           (sget<S, C>(stage, 5, 1, col) - sget<S, C>(stage, 8, 1, col)) +
+           (sget<S, C>(stage, 6, -1, col) - sget<S, C>(stage, 7, -1, col));
+}
+
+// ---- the fused step kernel ------------------------------------------------------------
+// collide row j of the tile from its stage and write it (and its ghosts)
+template <class S, class C>
+__device__ __forceinline__ void collide_row(const StepParams<C> &p, const S *src, S *__restrict__ dst, const S *st,
+                                            int x0, int lane, int j, const Mom<C> &mp, const Mom<C> &mc,
+                                            const Mom<C> &mn)
+{
+    const int i = x0 + lane;
+    const bool active = i < p.nx;
+    // axial neighbours of rho u_r on row j
+    C left = __shfl_up_sync(0xffffffffu, mc.jr, 1);
+    C right = __shfl_down_sync(0xffffffffu, mc.jr, 1);
+    if (lane == 0)
+        left = (i == 0) ? jr_beyond_inlet<S, C>(p, src, j) : stage_jr<S, C>(st, -1);
+    if (active && (lane == 31 || i == p.nx - 1))
+        right = (i == p.nx - 1) ? jr_beyond_outlet<S, C>(p, src, j, mc.jr) : stage_jr<S, C>(st, 32);
+    if (!active)
+        return;
+    C f[9], g[4], fo[9], go[4];
+    stage_pops<S, C>(st, lane, f, g);
+    const C inv_r = C(1) / (p.r0 + C(j) + C(0.5));
+    collide<C>(p, f, g, mc, inv_r, C(0.5) * (mn.jx - mp.jx), C(0.5) * (mn.jr - mp.jr), C(0.5) * (right - left),
+               C(0.5) * (mn.dT - mp.dT), fo, go);
+    S *o = dst + cell(p, 0, i, j);
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+        o[(int64_t)k * p.plane] = store_as<S, C>(fo[k]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        o[(int64_t)(9 + k) * p.plane] = store_as<S, C>(go[k]);
+    if (i == 0 || i == p.nx - 1 || j == 0 || j == p.nr - 1) {
+        C tf[9], tg[4];
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            tf[k] = fo[k];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            tg[k] = go[k];
+        write_ghosts<S, C>(p, dst, i, j, tf, tg, p.step + 1);
+    }
+}
+
+// One warp tile: columns x0..x0+31 of rows j0..j1-1.  Rows j0-1 (if any)
+// through min(j1, nr-1) are staged in order, NSTAGE - 2 rows ahead of the
+// one whose moments are being formed; row j is collided once the moments of
+// row j + 1 exist.
+template <class S, class C>
+__device__ __forceinline__ void step_tile(const StepParams<C> &p, const S *__restrict__ src, S *__restrict__ dst,
+                                          S *wsm, int tile, int lane)
+{
+    using Wn = Win<S>;
+    constexpr int D = NSTAGE - 2;
     const int strip = tile % p.nstrips;
     const int band = tile / p.nstrips;
     const int x0 = strip << 5;
-    const int i = x0 + lane;
-    const bool active = i < p.nx;
-    const int ic = active ? i : p.nx - 1;
     const int j0 = band * p.band;
     const int j1 = min(j0 + p.band, p.nr);
-    const S *__restrict__ src = static_cast<const S *>(p.src);
-    S *__restrict__ dst = static_cast<S *>(p.dst);
+    const int rfirst = j0 > 0 ? j0 - 1 : j0;
+    const int nrows = min(j1, p.nr - 1) - rfirst + 1;
 
-    C fc[9], gc[4];
-    pull<S, C>(p, src, ic, j0, fc, gc);
-    Mom<C> mc = moments<C>(fc, gc);
-    Mom<C> mp;
-    if (j0 > 0) {
-        C ft[9], gt[4];
-        pull<S, C>(p, src, ic, j0 - 1, ft, gt);
-        mp = moments<C>(ft, gt);
-    } else {
-        mp = ghost_bottom<C>(p, mc);
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+        if (t < nrows)
+            issue_row<S, C>(p, src, wsm + t * Wn::STAGE, x0, rfirst + t, lane);
+        cp_async_commit();
     }
-
+    Mom<C> mp, mc;
 #pragma unroll 1
-    for (int j = j0; j < j1; ++j) {
-        C fn[9], gn[4];
-        Mom<C> mn;
-        if (j + 1 < p.nr) {
-            pull<S, C>(p, src, ic, j + 1, fn, gn);
-            mn = moments<C>(fn, gn);
+    for (int idx = 0; idx < nrows; ++idx) {
+        __syncwarp();  // every lane is done with the stage refilled next
+        if (idx + D < nrows)
+            issue_row<S, C>(p, src, wsm + ((idx + D) % NSTAGE) * Wn::STAGE, x0, rfirst + idx + D, lane);
+        cp_async_commit();
+        cp_async_wait<D>();
+        __syncwarp();  // row idx has landed for every lane
+        const int r = rfirst + idx;
+        const S *st = wsm + (idx % NSTAGE) * Wn::STAGE;
+        C f[9], g[4];
+        stage_pops<S, C>(st, lane, f, g);
+        const Mom<C> mr = moments<C>(f, g);
+        if (r < j0) {
+            mp = mr;
+        } else if (r == j0) {
+            if (j0 == 0)
+                mp = ghost_bottom<C>(p, mr);
+            mc = mr;
         } else {
-#pragma unroll
-            for (int k = 0; k < 9; ++k)
-                fn[k] = C(0);
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                gn[k] = C(0);
-            mn = ghost_top<C>(p, mc);
+            collide_row<S, C>(p, src, dst, wsm + ((idx - 1) % NSTAGE) * Wn::STAGE, x0, lane, r - 1, mp, mc, mr);
+            mp = mc;
+            mc = mr;
         }
-
-        // axial neighbours of rho u_r on row j
-        C left = __shfl_up_sync(0xffffffffu, mc.jr, 1);
-        C right = __shfl_down_sync(0xffffffffu, mc.jr, 1);
-        if (lane == 0)
-            left = (i == 0) ? jr_beyond_inlet<S, C>(p, src, j) : jr_at<S, C>(p, src, i - 1, j);
-        if (active && (lane == 31 || i == p.nx - 1))
-            right = (i == p.nx - 1) ? jr_beyond_outlet<S, C>(p, src, j, mc.jr) : jr_at<S, C>(p, src, i + 1, j);
-
-        if (active) {
-            C fo[9], go[4];
-            const C inv_r = C(1) / (p.r0 + C(j) + C(0.5));
-            collide<C>(p, fc, gc, mc, inv_r, C(0.5) * (mn.jx - mp.jx), C(0.5) * (mn.jr - mp.jr),
-                       C(0.5) * (right - left), C(0.5) * (mn.dT - mp.dT), fo, go);
-            S *o = dst + cell(p, 0, i, j);
-#pragma unroll
-            for (int k = 0; k < 9; ++k)
-                o[(int64_t)k * p.plane] = store_as<S, C>(fo[k]);
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                o[(int64_t)(9 + k) * p.plane] = store_as<S, C>(go[k]);
-            if (i == 0 || i == p.nx - 1 || j == 0 || j == p.nr - 1) {
-                C tf[9], tg[4];
-#pragma unroll
-                for (int k = 0; k < 9; ++k)
-                    tf[k] = fo[k];
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    tg[k] = go[k];
-                write_ghosts<S, C>(p, dst, i, j, tf, tg, p.step + 1);
-            }
-        }
-
-        mp = mc;
-        mc = mn;
-#pragma unroll
-        for (int k = 0; k < 9; ++k)
-            fc[k] = fn[k];
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            gc[k] = gn[k];
     }
+    if (j1 == p.nr)
+        collide_row<S, C>(p, src, dst, wsm + ((nrows - 1) % NSTAGE) * Wn::STAGE, x0, lane, p.nr - 1, mp, mc,
+                          ghost_top<C>(p, mc));
+    cp_async_wait<0>();
+    __syncwarp();
+}
+
+template <class S>
+constexpr int step_smem_per_warp()
+{
+    return NSTAGE * Win<S>::STAGE * (int)sizeof(S);
+}
+
+template <class S, class C>
+__global__ void __launch_bounds__(256) step_kernel(const __grid_constant__ StepParams<C> p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpc = blockDim.x >> 5;
+    const int tile = blockIdx.x * wpc + warp;
+    if (tile >= p.ntiles)
+        return;  // whole warp
+    S *wsm = reinterpret_cast<S *>(smem_raw) + (size_t)warp * NSTAGE * Win<S>::STAGE;
+    step_tile<S, C>(p, static_cast<const S *>(p.src), static_cast<S *>(p.dst), wsm, tile, lane);
 }
 
 // ---- ghosts of a stored state (after it is set from outside) ------------------------

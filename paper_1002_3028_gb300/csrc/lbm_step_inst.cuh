@@ -7,14 +7,25 @@
 
 namespace lbm {
 
-cudaError_t LBM_CAT(launch_step_, LBM_TAG)(const StepParams<LBM_C> &p, int warps_per_cta, cudaStream_t s)
+cudaError_t LBM_CAT(launch_step_, LBM_TAG)(const StepParams<LBM_C> &p, int warps_per_cta, int ctas, cudaStream_t s)
 {
     if (p.ntiles <= 0)
         return cudaSuccess;
-    const int threads = 32 * warps_per_cta;
-    const int blocks = (p.ntiles + warps_per_cta - 1) / warps_per_cta;
-    step_kernel<LBM_S, LBM_C><<<blocks, threads, 0, s>>>(p);
+    const int smem = warps_per_cta * step_smem_per_warp<LBM_S>();
+    step_kernel<LBM_S, LBM_C><<<ctas, 32 * warps_per_cta, smem, s>>>(p);
     return cudaGetLastError();
+}
+
+// allows the dynamic shared memory of the widest CTA and reports how many
+// CTAs of the given width fit on one SM
+cudaError_t LBM_CAT(occupancy_step_, LBM_TAG)(int warps_per_cta, int *ctas_per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<LBM_S, LBM_C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         8 * step_smem_per_warp<LBM_S>());
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, step_kernel<LBM_S, LBM_C>, 32 * warps_per_cta,
+                                                         warps_per_cta * step_smem_per_warp<LBM_S>());
 }
 
 cudaError_t LBM_CAT(launch_fields_, LBM_TAG)(const StepParams<LBM_C> &p, void *out, int out_f64, cudaStream_t s)

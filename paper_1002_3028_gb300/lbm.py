@@ -93,9 +93,10 @@ def lib(build: bool = True):
             L.lbm_get_state.argtypes = [vp, vp, vp, vp]
             L.lbm_set_state.argtypes = [vp, vp, vp, i64, vp]
             L.lbm_set_launch.argtypes = [vp, i32, i32]
+            L.lbm_get_launch.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
             for name in ("lbm_required_bytes", "lbm_create", "lbm_set_inlet", "lbm_set_properties",
                          "lbm_step", "lbm_get_fields", "lbm_get_state", "lbm_set_state",
-                         "lbm_set_launch"):
+                         "lbm_set_launch", "lbm_get_launch"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -184,7 +185,14 @@ class Lattice:
                                           float(T_hi), _stream_ptr(stream)), "lbm_set_properties")
 
     def set_launch(self, band_rows: int = 0, warps_per_cta: int = 0):
+        """band_rows 0 = automatic (one wave of resident warps); warps 0 = unchanged."""
         _check(self._L.lbm_set_launch(self._h, band_rows, warps_per_cta), "lbm_set_launch")
+
+    def launch(self):
+        """(band rows, warps per CTA, CTAs) used by lbm_step."""
+        b, w, c = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(self._L.lbm_get_launch(self._h, C.byref(b), C.byref(w), C.byref(c)), "lbm_get_launch")
+        return b.value, w.value, c.value
 
     def step(self, n: int = 1, stream=None):
         _check(self._L.lbm_step(self._h, int(n), _stream_ptr(stream)), "lbm_step")

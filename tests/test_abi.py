@@ -13,7 +13,7 @@ def test_header_declares_the_boundary_calls():
     names = lbm.declared_symbols()
     for n in ("lbm_create", "lbm_set_inlet", "lbm_set_properties", "lbm_step", "lbm_get_fields",
               "lbm_destroy", "lbm_get_state", "lbm_set_state", "lbm_required_bytes",
-              "lbm_last_error", "lbm_get_step", "lbm_set_launch"):
+              "lbm_last_error", "lbm_get_step", "lbm_set_launch", "lbm_get_launch"):
         assert n in names
 
 
@@ -46,9 +46,10 @@ def test_desc_struct_matches_header_layout(tmp_path):
 
 def test_required_bytes_counts_two_buffers():
     """Two buffers of 13 planes; each plane has ghost rows -1 and nr and a
-    padded row pitch (32 leading elements, then columns 0..nx rounded up to 32)."""
+    padded row pitch (32 leading elements, columns 0..nx rounded up to 32,
+    32 trailing elements)."""
     cfg = I.LatticeConfig(nx=100, nr=40)
-    pitch = 32 + 128
+    pitch = 32 + 128 + 32
     for st, sz in (("f64", 8), ("f32", 4), ("f16", 2), ("bf16", 2)):
         n = lbm.required_bytes(cfg, st)
         two = 2 * 13 * pitch * (40 + 2) * sz
