@@ -94,7 +94,7 @@ typedef enum { LBM_BOTTOM_AXIS = 0, LBM_BOTTOM_WALL = 1 } lbm_bc_bottom;
  * axisym = 0 switches the axisymmetric sources off (the planar model).
  */
 typedef struct {
-    int32_t nx, nr;      /* 1 <= nx, nr; nx * nr <= 2^31 - 1 */
+    int32_t nx, nr;      /* 1 <= nx, nr < 2^20; 13 (nr + 2)(nx + 128) < 2^31 */
     int32_t storage;     /* lbm_storage */
     int32_t bc_in;       /* lbm_bc_in */
     int32_t bc_out;      /* lbm_bc_out */
@@ -179,7 +179,7 @@ LBM_API int lbm_set_state(lbm_lattice *h, const double *dev_f, const double *dev
 
 /*
  * Launch shape of the step kernel: CTAs of warps_per_cta warps (1..8), one
- * warp per tile of 32 columns x band_rows rows.  band_rows >= 1 fixes the
+ * warp per tile of 64 columns (32 for LBM_F64) x band_rows rows.  band_rows >= 1 fixes the
  * band height; 0 lets the library choose it from the number of warps the GPU
  * holds at once (the default).  warps_per_cta == 0 keeps the current value.
  * Results do not depend on the launch shape.

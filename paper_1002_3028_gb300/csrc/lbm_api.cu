@@ -36,6 +36,10 @@ constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
+// lattice columns per warp strip of the step kernel: 32 nodes per lane-slot,
+// two per lane in FP32 arithmetic
+int strip_cols(int storage) { return storage == LBM_F64 ? 32 : 64; }
+
 size_t storage_bytes(int storage)
 {
     switch (storage) {
@@ -49,10 +53,10 @@ size_t storage_bytes(int storage)
 
 // row pitch: PAD_COLS leading elements (the last of them is ghost column
 // -1), then columns 0..nx (nx is the other ghost column) rounded up to a
-// multiple of 32, then 32 more so a warp's staged window (its 32 columns and
-// a 16-byte halo on each side) never leaves the row; every row and every
-// warp segment starts on a 64-byte boundary
-int row_pitch(int nx) { return lbm::PAD_COLS + (nx + 1 + 31) / 32 * 32 + 32; }
+// multiple of 64, then 32 more so a warp's staged window (its 32 or 64
+// columns and a 16-byte halo on each side) never leaves the row; every row
+// and every warp strip starts on a 64-byte boundary
+int row_pitch(int nx) { return lbm::PAD_COLS + (nx + 1 + 63) / 64 * 64 + 32; }
 
 struct Layout {
     int pitch;
@@ -76,6 +80,9 @@ int check_desc(const lbm_desc *d)
         return fail(LBM_ERR_INVALID_ARG, "nr must be below 2^20 (inlet noise counter)");
     if (storage_bytes(d->storage) == 0)
         return fail(LBM_ERR_INVALID_ARG, "unknown storage type %d", d->storage);
+    // the step kernel addresses a population buffer with 32-bit element offsets
+    if (13 * (int64_t)row_pitch(d->nx) * (d->nr + 2) >= INT32_MAX)
+        return fail(LBM_ERR_INVALID_ARG, "lattice %d x %d exceeds 13 * (nr + 2) * pitch < 2^31 elements", d->nx, d->nr);
     if (d->bc_in < 0 || d->bc_in > 1 || d->bc_out < 0 || d->bc_out > 2 || d->bc_top < 0 || d->bc_top > 1 ||
         d->bc_bottom < 0 || d->bc_bottom > 1)
         return fail(LBM_ERR_INVALID_ARG, "unknown boundary kind");
@@ -154,7 +161,7 @@ lbm::StepParams<C> make_params(const lbm_lattice *h, const C *u_in, const C *T_i
     p.bc_bottom = d.bc_bottom;
     p.axisym = d.axisym ? 1 : 0;
     p.band = h->band_eff;
-    p.nstrips = (d.nx + 31) / 32;
+    p.nstrips = (d.nx + strip_cols(d.storage) - 1) / strip_cols(d.storage);
     const int nbands = (d.nr + h->band_eff - 1) / h->band_eff;
     p.ntiles = p.nstrips * nbands;
     p.ntab = h->ntab;
@@ -190,10 +197,10 @@ lbm::StepParams<float> params_f(const lbm_lattice *h)
                               h->at<float>(h->L.off_nu_f), h->at<float>(h->L.off_al_f));
 }
 
-// Launch shape of the step kernel: one warp per 32-column x band-row tile,
-// all tiles in one grid.  The automatic band height keeps about four tiles
+// Launch shape of the step kernel: one warp per strip x band-row tile,
+// all tiles in one grid.  The automatic band height keeps about eight tiles
 // per resident warp (so CTAs start and finish at staggered times and the
-// last wave is short), bounded to 4..32 rows (each band pulls two extra
+// last wave is short), bounded to 4..16 rows (each band pulls two extra
 // halo rows).
 int plan_launch(lbm_lattice *h)
 {
@@ -210,13 +217,13 @@ int plan_launch(lbm_lattice *h)
     if (per_sm < 1)
         return fail(LBM_ERR_INVALID_ARG, "a CTA of %d warps does not fit on an SM", h->warps);
     const int resident_warps = per_sm * std::max(1, h->sms) * h->warps;
-    const int nstrips = (h->d.nx + 31) / 32;
+    const int nstrips = (h->d.nx + strip_cols(h->d.storage) - 1) / strip_cols(h->d.storage);
     if (h->band > 0) {
         h->band_eff = h->band;
     } else {
-        const int64_t want_tiles = 4 * (int64_t)resident_warps;
+        const int64_t want_tiles = 8 * (int64_t)resident_warps;
         const int64_t band = ((int64_t)h->d.nr * nstrips + want_tiles - 1) / want_tiles;
-        h->band_eff = (int)std::min<int64_t>(32, std::max<int64_t>(4, band));
+        h->band_eff = (int)std::min<int64_t>(16, std::max<int64_t>(4, band));
     }
     const int64_t ntiles = (int64_t)nstrips * ((h->d.nr + h->band_eff - 1) / h->band_eff);
     h->ctas = (int)((ntiles + h->warps - 1) / h->warps);
@@ -315,7 +322,7 @@ int lbm_create(const lbm_desc *d, void *dev_mem, size_t bytes, lbm_lattice **out
     h->cur = 0;
     h->step = 0;
     h->band = 0;
-    h->warps = 4;
+    h->warps = 2;
     cudaGetDevice(&h->device);
     h->sms = 1;
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);

@@ -6,11 +6,11 @@
 // Storage.  13 planes (9 f, 4 g); each plane holds nr + 2 rows of `pitch`
 // values: row -1 (ghost), rows 0..nr-1, row nr (ghost); in every row the
 // lattice column i sits at element i + PAD_COLS, so columns -1 and nx are
-// ghosts and every warp's 32-column segment starts on an aligned boundary.
-// Every value is the deviation from the rest state, f_k - w_k rho0 and
-// g_k - T0/4.  The arithmetic type C is double for FP64 storage and float
-// for FP32/FP16/BF16; all collision arithmetic runs on deviations, so the
-// rounding of a stored value is relative to its (small) departure from rest.
+// ghosts and every warp's strip starts on an aligned boundary.  Every value
+// is the deviation from the rest state, f_k - w_k rho0 and g_k - T0/4.  The
+// arithmetic type C is double for FP64 storage and float for FP32/FP16/BF16;
+// all collision arithmetic runs on deviations, so the rounding of a stored
+// value is relative to its (small) departure from rest.
 //
 // Boundaries as ghosts.  The boundary rules only ever pick, for a pulled
 // source outside the lattice, a value computed from the post-collision
@@ -21,14 +21,16 @@
 // every node, with no branch.  The radial rule is applied before the axial
 // one, exactly as in the rules' definition.
 //
-// Work split of the step kernel.  One warp owns a strip of 32 consecutive
-// columns and marches up a band of rows.  The populations each row pulls are
-// staged in the warp's shared-memory ring by asynchronous copies issued two
-// rows ahead; from a landed row the warp forms the Eq. 2 moments and
-// collides the row below, whose radial neighbours' moments (same time level)
-// it already holds.  The axial neighbours' rho u_r comes from the adjacent
-// lanes by warp shuffle and, for the two columns beside the strip, from the
-// staged window's halo.
+// Work split of the step kernel.  One warp owns a strip of 32 NV consecutive
+// columns (NV = 2 nodes per lane in FP32 arithmetic, at columns x0 + lane and
+// x0 + 32 + lane, computed together with the paired FP32x2 instructions;
+// NV = 1 in FP64) and marches up a band of rows.  The populations each row
+// pulls are staged in the warp's shared-memory ring by asynchronous copies
+// issued two rows ahead; from a landed row the warp forms the Eq. 2 moments
+// and collides the row below, whose radial neighbours' moments (same time
+// level) it already holds.  The axial neighbours' rho u_r come from the
+// adjacent columns by warp shuffle and, for the two columns beside the
+// strip, from the staged window's halo.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -54,6 +56,10 @@ __host__ __device__ constexpr int ex4(int k) { return k == 0 ? 1 : (k == 2 ? -1 
 __host__ __device__ constexpr int ey4(int k) { return k == 1 ? 1 : (k == 3 ? -1 : 0); }
 template <class C> __host__ __device__ constexpr C w9(int k) { return k == 0 ? C(4) / C(9) : (k <= 4 ? C(1) / C(9) : C(1) / C(36)); }
 
+// nodes per lane of the step kernel for an arithmetic type
+template <class C> struct NodesPerLane { static constexpr int value = 1; };
+template <> struct NodesPerLane<float> { static constexpr int value = 2; };
+
 // ---- kernel parameters -------------------------------------------------------
 template <class C>
 struct StepParams {
@@ -63,7 +69,7 @@ struct StepParams {
     int nx, nr, pitch;
     int bc_in, bc_out, bc_top, bc_bottom, axisym;
     int band;         // rows per warp tile
-    int nstrips;      // ceil(nx / 32)
+    int nstrips;      // ceil(nx / (32 NV))
     int ntiles;       // nstrips * ceil(nr / band)
     int ntab;
     int64_t step;     // time index of the step that reads src
@@ -107,6 +113,73 @@ template <class S, class C>
 __device__ __forceinline__ C ld(const StepParams<C> &p, const S *src, int q, int i, int j)
 {
     return load_as<S, C>(src + cell(p, q, i, j));
+}
+
+// ---- NV nodes of one lane as one value ---------------------------------------
+// Vec<C, 1> is a scalar; Vec<float, 2> holds two nodes and maps +, -, * and
+// fma onto the paired FP32x2 instructions of sm_100 and later.
+template <class C, int N> struct Vec;
+
+template <class C>
+struct Vec<C, 1> {
+    C x;
+    __device__ __forceinline__ Vec() {}
+    __device__ __forceinline__ explicit Vec(C s) : x(s) {}
+    __device__ __forceinline__ C operator[](int) const { return x; }
+    __device__ __forceinline__ void set(int, C v) { x = v; }
+};
+template <class C> __device__ __forceinline__ Vec<C, 1> operator+(Vec<C, 1> a, Vec<C, 1> b) { return Vec<C, 1>(a.x + b.x); }
+template <class C> __device__ __forceinline__ Vec<C, 1> operator-(Vec<C, 1> a, Vec<C, 1> b) { return Vec<C, 1>(a.x - b.x); }
+template <class C> __device__ __forceinline__ Vec<C, 1> operator*(Vec<C, 1> a, Vec<C, 1> b) { return Vec<C, 1>(a.x * b.x); }
+template <class C> __device__ __forceinline__ Vec<C, 1> operator-(Vec<C, 1> a) { return Vec<C, 1>(-a.x); }
+template <class C> __device__ __forceinline__ Vec<C, 1> vfma(Vec<C, 1> a, Vec<C, 1> b, Vec<C, 1> c) { return Vec<C, 1>(a.x * b.x + c.x); }
+
+template <>
+struct Vec<float, 2> {
+    float2 v;
+    __device__ __forceinline__ Vec() {}
+    __device__ __forceinline__ explicit Vec(float s) : v(make_float2(s, s)) {}
+    __device__ __forceinline__ explicit Vec(float2 a) : v(a) {}
+    __device__ __forceinline__ float operator[](int c) const { return c ? v.y : v.x; }
+    __device__ __forceinline__ void set(int c, float a)
+    {
+        if (c)
+            v.y = a;
+        else
+            v.x = a;
+    }
+};
+using F2 = Vec<float, 2>;
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(make_float2(-a.v.x, -a.v.y)); }
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+
+template <class C, int N> __device__ __forceinline__ Vec<C, N> operator*(C s, Vec<C, N> a) { return Vec<C, N>(s) * a; }
+template <class C, int N> __device__ __forceinline__ Vec<C, N> operator+(C s, Vec<C, N> a) { return Vec<C, N>(s) + a; }
+template <class C, int N> __device__ __forceinline__ Vec<C, N> operator-(Vec<C, N> a, C s) { return a - Vec<C, N>(s); }
+template <class C, int N> __device__ __forceinline__ Vec<C, N> operator-(C s, Vec<C, N> a) { return Vec<C, N>(s) - a; }
+
+// component-wise reciprocal and square root
+template <class C, int N>
+__device__ __forceinline__ Vec<C, N> vrcp(Vec<C, N> a)
+{
+    Vec<C, N> r;
+#pragma unroll
+    for (int c = 0; c < N; ++c)
+        r.set(c, C(1) / a[c]);
+    return r;
+}
+
+template <class C, int N>
+__device__ __forceinline__ Vec<C, N> vsqrt(Vec<C, N> a)
+{
+    Vec<C, N> r;
+#pragma unroll
+    for (int c = 0; c < N; ++c)
+        r.set(c, sqrt(a[c]));
+    return r;
 }
 
 // ---- inlet noise: SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) ---------------
@@ -153,16 +226,23 @@ __device__ __forceinline__ C feq_unit(int k, C ux, C ur)
 }
 
 // ---- boundary ghosts -------------------------------------------------------------
-// Node (i, j) on the lattice edge, with post-collision deviations fo/go,
-// writes every ghost cell whose value the boundary rules take from it.
-// t is the time index of the step that will pull these ghosts (inlet noise).
-// Writers of distinct ghost cells are distinct nodes, except where two
-// rules give the same bounce-back value to the same cell.
+// Node (i, j) on the lattice edge, whose post-collision deviations are
+// already stored in buf, writes every ghost cell of buf whose value the
+// boundary rules take from it.  t is the time index of the step that will
+// pull these ghosts (inlet noise).  Writers of distinct ghost cells are
+// distinct nodes, except where two rules give the same bounce-back value to
+// the same cell.
 template <class S, class C>
-__device__ __noinline__ void write_ghosts(const StepParams<C> &p, S *dst, int i, int j, const C *fo, const C *go,
-                                          int64_t t)
+__device__ __noinline__ void write_ghosts(const StepParams<C> &p, S *buf, int i, int j, int64_t t)
 {
     const int nx = p.nx, nr = p.nr;
+    C fo[9], go[4];
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+        fo[k] = load_as_shared<S, C>(buf + cell(p, k, i, j));  // plain load: this thread stored it
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        go[k] = load_as_shared<S, C>(buf + cell(p, 9 + k, i, j));
     C drho = C(0), jx = C(0), jr = C(0);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -172,7 +252,7 @@ __device__ __noinline__ void write_ghosts(const StepParams<C> &p, S *dst, int i,
     }
     const C rho = p.rho0 + drho;
     const C ux = jx / rho, ur = jr / rho;
-    auto W = [&](int q, int ci, int cj, C v) { dst[cell(p, q, ci, cj)] = store_as<S, C>(v); };
+    auto W = [&](int q, int ci, int cj, C v) { buf[cell(p, q, ci, cj)] = store_as<S, C>(v); };
     // zero-gradient copy of this node held at rho0
     auto openc = [&](int k) -> C { return fo[k] - drho * feq_unit<C>(k, ux, ur); };
     // inlet equilibrium at this node's density, this row's prescribed velocity
@@ -279,15 +359,15 @@ __device__ __forceinline__ void pull(const StepParams<C> &p, const S *src, int i
         g[k] = ld<S, C>(p, src, 9 + k, i - ex4(k), j - ey4(k));
 }
 
-template <class C>
+template <class V>
 struct Mom {
-    C drho, jx, jr, dT;  // rho - rho0, rho u_x, rho u_r, T - T0
+    V drho, jx, jr, dT;  // rho - rho0, rho u_x, rho u_r, T - T0
 };
 
-template <class C>
-__device__ __forceinline__ Mom<C> moments(const C (&f)[9], const C (&g)[4])
+template <class V>
+__device__ __forceinline__ Mom<V> moments(const V (&f)[9], const V (&g)[4])
 {
-    Mom<C> m;
+    Mom<V> m;
     m.drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
     m.jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
     m.jr = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
@@ -296,26 +376,26 @@ __device__ __forceinline__ Mom<C> moments(const C (&f)[9], const C (&g)[4])
 }
 
 // moments of the ghost row below row 0 / above row nr - 1 (central differences)
-template <class C>
-__device__ __forceinline__ Mom<C> ghost_bottom(const StepParams<C> &p, Mom<C> m)
+template <class C, class V>
+__device__ __forceinline__ Mom<V> ghost_bottom(const StepParams<C> &p, Mom<V> m)
 {
     if (p.bc_bottom == BOTTOM_AXIS) {
         m.jr = -m.jr;  // rho u_r odd, rho u_x and T even across the axis
     } else {
         m.jx = -m.jx;
         m.jr = -m.jr;
-        m.dT = C(2) * p.dT_bottom - m.dT;
+        m.dT = V(C(2) * p.dT_bottom) - m.dT;
     }
     return m;
 }
 
-template <class C>
-__device__ __forceinline__ Mom<C> ghost_top(const StepParams<C> &p, Mom<C> m)
+template <class C, class V>
+__device__ __forceinline__ Mom<V> ghost_top(const StepParams<C> &p, Mom<V> m)
 {
     if (p.bc_top == TOP_WALL) {
         m.jx = -m.jx;
         m.jr = -m.jr;
-        m.dT = C(2) * p.dT_top - m.dT;
+        m.dT = V(C(2) * p.dT_top) - m.dT;
     }
     return m;
 }
@@ -355,85 +435,97 @@ __device__ __forceinline__ void properties(const StepParams<C> &p, C T, C &nu, C
     al = a0 + fr * (a1 - a0);
 }
 
-// ---- collision of one node (right-hand side of Eq. 1) -------------------------------
+// ---- collision of NV nodes (right-hand side of Eq. 1) -------------------------------
 // d_* are central differences: d_r(rho u_x), d_r(rho u_r), d_x(rho u_r), d_r T.
 // Equilibrium deviations are formed pairwise: with j = rho u,
 //   f_eq_k - w_k rho0 = w_k (A + 3 e_k.j + 9/2 (e_k.j)(e_k.u)),  A = drho - 3/2 j.u,
 // and opposite directions share the quadratic term.
-template <class C>
-__device__ __forceinline__ void collide(const StepParams<C> &p, const C (&f)[9], const C (&g)[4], const Mom<C> &m,
-                                        C inv_r, C d_rjx, C d_rjr, C d_xjr, C d_rT, C (&fo)[9], C (&go)[4])
+template <class C, class V>
+__device__ __forceinline__ void collide(const StepParams<C> &p, const V (&f)[9], const V (&g)[4], const Mom<V> &m,
+                                        C inv_r, V d_rjx, V d_rjr, V d_xjr, V d_rT, V (&fo)[9], V (&go)[4])
 {
+    constexpr int N = sizeof(V) / sizeof(C);
     constexpr C third = C(1) / C(3);
     constexpr C sixth = C(1) / C(6);
     constexpr C w0 = C(4) / C(9), w1 = C(1) / C(9), w2 = C(1) / C(36);
-    const C rho = p.rho0 + m.drho;
-    const C inv_rho = C(1) / rho;
-    const C ux = m.jx * inv_rho, ur = m.jr * inv_rho;
-    const C T = p.T0 + m.dT;
-    C nu, al;
-    properties<C>(p, T, nu, al);
-    const C tau_nu = C(0.5) + C(3) * nu;
+    const V rho = p.rho0 + m.drho;
+    const V inv_rho = vrcp(rho);
+    const V ux = m.jx * inv_rho, ur = m.jr * inv_rho;
+    const V T = p.T0 + m.dT;
+    V nu, al;
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        C a, b;
+        properties<C>(p, T[c], a, b);
+        nu.set(c, a);
+        al.set(c, b);
+    }
+    const V tau_nu = vfma(V(C(3)), nu, V(C(0.5)));
 
-    const C A = m.drho - C(1.5) * (m.jx * ux + m.jr * ur);
-    const C jp = m.jx + m.jr, up = ux + ur, jm = m.jx - m.jr, um = ux - ur;
-    const C qx = A + C(4.5) * m.jx * ux, qr = A + C(4.5) * m.jr * ur;
-    const C qp = A + C(4.5) * jp * up, qm = A + C(4.5) * jm * um;
-    C fneq[9];
+    const V A = m.drho - C(1.5) * vfma(m.jx, ux, m.jr * ur);
+    const V jp = m.jx + m.jr, up = ux + ur, jm = m.jx - m.jr, um = ux - ur;
+    const V qx = vfma(C(4.5) * m.jx, ux, A), qr = vfma(C(4.5) * m.jr, ur, A);
+    const V qp = vfma(C(4.5) * jp, up, A), qm = vfma(C(4.5) * jm, um, A);
+    const V jx3 = C(3) * m.jx, jr3 = C(3) * m.jr, jp3 = C(3) * jp, jm3 = C(3) * jm;
+    V fneq[9];
     fneq[0] = f[0] - w0 * A;
-    fneq[1] = f[1] - w1 * (qx + C(3) * m.jx);
-    fneq[3] = f[3] - w1 * (qx - C(3) * m.jx);
-    fneq[2] = f[2] - w1 * (qr + C(3) * m.jr);
-    fneq[4] = f[4] - w1 * (qr - C(3) * m.jr);
-    fneq[5] = f[5] - w2 * (qp + C(3) * jp);  // e = (1, 1)
-    fneq[7] = f[7] - w2 * (qp - C(3) * jp);  // e = (-1, -1)
-    fneq[8] = f[8] - w2 * (qm + C(3) * jm);  // e = (1, -1)
-    fneq[6] = f[6] - w2 * (qm - C(3) * jm);  // e = (-1, 1)
+    fneq[1] = f[1] - w1 * (qx + jx3);
+    fneq[3] = f[3] - w1 * (qx - jx3);
+    fneq[2] = f[2] - w1 * (qr + jr3);
+    fneq[4] = f[4] - w1 * (qr - jr3);
+    fneq[5] = f[5] - w2 * (qp + jp3);  // e = (1, 1)
+    fneq[7] = f[7] - w2 * (qp - jp3);  // e = (-1, -1)
+    fneq[8] = f[8] - w2 * (qm + jm3);  // e = (1, -1)
+    fneq[6] = f[6] - w2 * (qm - jm3);  // e = (-1, 1)
 
     // stress Q_ij of Eq. 4 and the Smagorinsky relaxation time
-    const C dsum = (fneq[5] + fneq[6]) + (fneq[7] + fneq[8]);
-    const C Qxx = (fneq[1] + fneq[3]) + dsum;
-    const C Qrr = (fneq[2] + fneq[4]) + dsum;
-    const C Qxr = (fneq[5] - fneq[6]) + (fneq[7] - fneq[8]);
-    const C Qn = sqrt(C(2) * (Qxx * Qxx + C(2) * Qxr * Qxr + Qrr * Qrr));
-    const C tau = C(0.5) * (tau_nu + sqrt(tau_nu * tau_nu + p.cs2_18 * Qn * inv_rho));  // Eq. 4
-    const C nu_t = (tau - tau_nu) * third;                                               // Eq. 3
-    const C al_tot = al + nu_t * p.inv_prt;                                              // Eq. 5
-    const C tau_a = C(0.5) + C(2) * al_tot;
-    const C nu_tot = (tau - C(0.5)) * third;
+    const V dsum = (fneq[5] + fneq[6]) + (fneq[7] + fneq[8]);
+    const V Qxx = (fneq[1] + fneq[3]) + dsum;
+    const V Qrr = (fneq[2] + fneq[4]) + dsum;
+    const V Qxr = (fneq[5] - fneq[6]) + (fneq[7] - fneq[8]);
+    const V Qn = vsqrt(C(2) * vfma(Qxx, Qxx, vfma(C(2) * Qxr, Qxr, Qrr * Qrr)));
+    const V tau = C(0.5) * (tau_nu + vsqrt(vfma(tau_nu, tau_nu, V(p.cs2_18) * Qn * inv_rho)));  // Eq. 4
+    const V nu_t = (tau - tau_nu) * V(third);                                                   // Eq. 3
+    const V al_tot = vfma(nu_t, V(p.inv_prt), al);                                              // Eq. 5
+    const V tau_a = vfma(V(C(2)), al_tot, V(C(0.5)));
+    const V nu_tot = (tau - C(0.5)) * V(third);
 
     // axisymmetric sources
-    C F1 = C(0), F2x = C(0), F2r = C(0), S = C(0);
+    V F1(C(0)), F2x(C(0)), F2r(C(0)), S(C(0));
     if (p.axisym) {
-        const C nr_ = nu_tot * inv_r;
-        F1 = -m.jr * inv_r;
-        F2x = -m.jx * ur * inv_r + nr_ * (d_rjx + d_xjr);
-        F2r = -m.jr * ur * inv_r + nr_ * (d_rjr + d_rjr) - C(2) * nr_ * m.jr * inv_r;
-        S = -T * ur * inv_r + al_tot * inv_r * d_rT;
+        const V ir(inv_r);
+        const V nr_ = nu_tot * ir;
+        F1 = -(m.jr * ir);
+        F2x = vfma(nr_, d_rjx + d_xjr, -(m.jx * ur * ir));
+        F2r = vfma(nr_, (d_rjr + d_rjr) - C(2) * m.jr * ir, -(m.jr * ur * ir));
+        S = vfma(al_tot * ir, d_rT, -(T * ur * ir));
     }
 
-    const C omega = C(1) / tau;
-    const C omega_a = C(1) / tau_a;
-    const C sx = F2x * sixth, sr = F2r * sixth;
-    const C s1 = w1 * F1, s2 = w2 * F1;
-    fo[0] = f[0] - omega * fneq[0] + w0 * F1;
-    fo[1] = f[1] - omega * fneq[1] + (s1 + sx);
-    fo[3] = f[3] - omega * fneq[3] + (s1 - sx);
-    fo[2] = f[2] - omega * fneq[2] + (s1 + sr);
-    fo[4] = f[4] - omega * fneq[4] + (s1 - sr);
-    fo[5] = f[5] - omega * fneq[5] + (s2 + (sx + sr));
-    fo[7] = f[7] - omega * fneq[7] + (s2 - (sx + sr));
-    fo[8] = f[8] - omega * fneq[8] + (s2 + (sx - sr));
-    fo[6] = f[6] - omega * fneq[6] + (s2 - (sx - sr));
+    const V omega = vrcp(tau);
+    const V omega_a = vrcp(tau_a);
+    const V sx = F2x * V(sixth), sr = F2r * V(sixth);
+    const V s1 = w1 * F1, s2 = w2 * F1;
+    const V nomega = -omega;
+    fo[0] = vfma(nomega, fneq[0], f[0] + w0 * F1);
+    fo[1] = vfma(nomega, fneq[1], f[1] + (s1 + sx));
+    fo[3] = vfma(nomega, fneq[3], f[3] + (s1 - sx));
+    fo[2] = vfma(nomega, fneq[2], f[2] + (s1 + sr));
+    fo[4] = vfma(nomega, fneq[4], f[4] + (s1 - sr));
+    fo[5] = vfma(nomega, fneq[5], f[5] + (s2 + (sx + sr)));
+    fo[7] = vfma(nomega, fneq[7], f[7] + (s2 - (sx + sr)));
+    fo[8] = vfma(nomega, fneq[8], f[8] + (s2 + (sx - sr)));
+    fo[6] = vfma(nomega, fneq[6], f[6] + (s2 - (sx - sr)));
 
     // D2Q4: g_eq_k - T0/4 = dT/4 + (T/2) e_k.u
-    const C gd = C(0.25) * m.dT;
-    const C hx = C(0.5) * T * ux, hr = C(0.5) * T * ur;
-    const C qS = C(0.25) * S;
-    go[0] = g[0] - omega_a * (g[0] - (gd + hx)) + qS;
-    go[2] = g[2] - omega_a * (g[2] - (gd - hx)) + qS;
-    go[1] = g[1] - omega_a * (g[1] - (gd + hr)) + qS;
-    go[3] = g[3] - omega_a * (g[3] - (gd - hr)) + qS;
+    const V gd = C(0.25) * m.dT;
+    const V hT = C(0.5) * T;
+    const V hx = hT * ux, hr = hT * ur;
+    const V qS = C(0.25) * S;
+    const V nomega_a = -omega_a;
+    go[0] = vfma(nomega_a, g[0] - (gd + hx), g[0] + qS);
+    go[2] = vfma(nomega_a, g[2] - (gd - hx), g[2] + qS);
+    go[1] = vfma(nomega_a, g[1] - (gd + hr), g[1] + qS);
+    go[3] = vfma(nomega_a, g[3] - (gd - hr), g[3] + qS);
 }
 
 // rho u_r just beyond the inlet end (ghost moment of the central difference)
@@ -457,18 +549,21 @@ __device__ __forceinline__ C jr_beyond_outlet(const StepParams<C> &p, const S *s
 }
 
 // ---- shared-memory staging of pulled rows -------------------------------------------
-// Each warp owns a ring of NSTAGE stages.  A stage holds, for one lattice row
+// Each warp owns a ring of NSTAGE<NV> stages (3 for two nodes per lane, 4
+// for one: the stage sizes differ, the shared memory per SM does not).  A
+// stage holds, for one lattice row
 // r and each plane q, the window of source row r - e_qy over source columns
-// x0 - H .. x0 + 31 + H (H = one 16-byte chunk of elements), copied with
-// asynchronous 16-byte copies spread over the warp's lanes.  Lane l then
-// reads population q of node (x0 + l, r) at window index l + H - e_qx.
-constexpr int NSTAGE = 4;
+// x0 - H .. x0 + 32 NV - 1 + H (H = one 16-byte chunk of elements), copied
+// with asynchronous 16-byte copies spread over the warp's lanes.  Node
+// column c of the strip (0 .. 32 NV - 1) reads population q at window index
+// c + H - e_qx.
+template <int NV> struct Stages { static constexpr int value = NV == 1 ? 4 : 3; };
 
-template <class S>
+template <class S, int NV>
 struct Win {
     static constexpr int E = 16 / (int)sizeof(S);  // elements per 16-byte chunk
     static constexpr int H = E;                    // halo elements on each side
-    static constexpr int W = 32 + 2 * H;           // window length
+    static constexpr int W = 32 * NV + 2 * H;      // window length
     static constexpr int CH = W / E;               // chunks per plane
     static constexpr int STAGE = 13 * W;           // elements per stage
 };
@@ -496,159 +591,203 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// start the copies of lattice row r into one stage
-template <class S, class C>
-__device__ __forceinline__ void issue_row(const StepParams<C> &p, const S *src, S *stage, int x0, int r, int lane)
+// The chunks one lane copies for every row of a tile: their element offsets
+// within a row's pull (plane, source-row shift and column); chunk
+// t = lane + 32 m lands at stage element t * E.  Offsets are 32-bit (the
+// library caps the lattice so that 13 planes stay below 2^31 elements).
+template <class S, int NV>
+struct CopyPlan {
+    static constexpr int TOTAL = 13 * Win<S, NV>::CH;
+    static constexpr int PER_LANE = (TOTAL + 31) / 32;
+    int goff[PER_LANE];
+};
+
+template <class S, int NV, class C>
+__device__ __forceinline__ CopyPlan<S, NV> make_copy_plan(const StepParams<C> &p, int x0, int lane)
 {
-    using Wn = Win<S>;
-    constexpr int total = 13 * Wn::CH;
+    using Wn = Win<S, NV>;
+    CopyPlan<S, NV> cp;
 #pragma unroll
-    for (int m = 0; m < (total + 31) / 32; ++m) {
-        const int t = lane + 32 * m;
-        if (t < total) {
-            const int q = t / Wn::CH;
-            const int c = t - q * Wn::CH;
-            cp_async16(stage + q * Wn::W + c * Wn::E, src + cell(p, q, x0 - Wn::H + c * Wn::E, r - plane_ey(q)));
-        }
+    for (int m = 0; m < CopyPlan<S, NV>::PER_LANE; ++m) {
+        const int t = min(lane + 32 * m, CopyPlan<S, NV>::TOTAL - 1);
+        const int q = t / Wn::CH;
+        const int c = t - q * Wn::CH;
+        cp.goff[m] = q * (int)p.plane - plane_ey(q) * p.pitch + (x0 - Wn::H + c * Wn::E + PAD_COLS);
     }
+    return cp;
 }
 
-// population q of lane `col` (0..31, or -1 / 32 for the columns beside the strip)
-template <class S, class C>
+// start the copies of lattice row r into one stage
+template <class S, int NV, class C>
+__device__ __forceinline__ void issue_row(const StepParams<C> &p, const S *src, S *stage, const CopyPlan<S, NV> &cp,
+                                          int r, int lane)
+{
+    const int row = (r + 1) * p.pitch;
+#pragma unroll
+    for (int m = 0; m < CopyPlan<S, NV>::PER_LANE; ++m)
+        if (lane + 32 * m < CopyPlan<S, NV>::TOTAL)
+            cp_async16(stage + (lane + 32 * m) * Win<S, NV>::E, src + (unsigned)(row + cp.goff[m]));
+}
+
+// population q of strip column col (-1 and 32 NV are the columns beside the strip)
+template <class S, int NV, class C>
 __device__ __forceinline__ C sget(const S *stage, int q, int ex, int col)
 {
-    using Wn = Win<S>;
+    using Wn = Win<S, NV>;
     return load_as_shared<S, C>(stage + q * Wn::W + col + Wn::H - ex);
 }
 
-template <class S, class C>
-__device__ __forceinline__ void stage_pops(const S *stage, int lane, C (&f)[9], C (&g)[4])
+template <class S, int NV, class C>
+__device__ __forceinline__ void stage_pops(const S *stage, int lane, Vec<C, NV> (&f)[9], Vec<C, NV> (&g)[4])
 {
 #pragma unroll
-    for (int k = 0; k < 9; ++k)
-        f[k] = sget<S, C>(stage, k, ex9(k), lane);
+    for (int c = 0; c < NV; ++c) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-        g[k] = sget<S, C>(stage, 9 + k, ex4(k), lane);
+        for (int k = 0; k < 9; ++k)
+            f[k].set(c, sget<S, NV, C>(stage, k, ex9(k), lane + 32 * c));
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            g[k].set(c, sget<S, NV, C>(stage, 9 + k, ex4(k), lane + 32 * c));
+    }
 }
 
-// rho u_r of the streamed populations in window column col of a stage
-template <class S, class C>
+// rho u_r of the streamed populations in strip column col of a stage
+template <class S, int NV, class C>
 __device__ __forceinline__ C stage_jr(const S *stage, int col)
 {
-    return (sget<S, C>(stage, 2, 0, col) - sget<S, C>(stage, 4, 0, col)) +
-           (sget<S, C>(stage, 5, 1, col) - sget<S, C>(stage, 8, 1, col)) +
-           (sget<S, C>(stage, 6, -1, col) - sget<S, C>(stage, 7, -1, col));
+    return (sget<S, NV, C>(stage, 2, 0, col) - sget<S, NV, C>(stage, 4, 0, col)) +
+           (sget<S, NV, C>(stage, 5, 1, col) - sget<S, NV, C>(stage, 8, 1, col)) +
+           (sget<S, NV, C>(stage, 6, -1, col) - sget<S, NV, C>(stage, 7, -1, col));
 }
 
 // ---- the fused step kernel ------------------------------------------------------------
 // collide row j of the tile from its stage and write it (and its ghosts)
-template <class S, class C>
+template <class S, int NV, class C>
 __device__ __forceinline__ void collide_row(const StepParams<C> &p, const S *src, S *__restrict__ dst, const S *st,
-                                            int x0, int lane, int j, const Mom<C> &mp, const Mom<C> &mc,
-                                            const Mom<C> &mn)
+                                            int x0, int lane, int j, const Mom<Vec<C, NV>> &mp,
+                                            const Mom<Vec<C, NV>> &mc, const Mom<Vec<C, NV>> &mn)
 {
-    const int i = x0 + lane;
-    const bool active = i < p.nx;
-    // axial neighbours of rho u_r on row j
-    C left = __shfl_up_sync(0xffffffffu, mc.jr, 1);
-    C right = __shfl_down_sync(0xffffffffu, mc.jr, 1);
-    if (lane == 0)
-        left = (i == 0) ? jr_beyond_inlet<S, C>(p, src, j) : stage_jr<S, C>(st, -1);
-    if (active && (lane == 31 || i == p.nx - 1))
-        right = (i == p.nx - 1) ? jr_beyond_outlet<S, C>(p, src, j, mc.jr) : stage_jr<S, C>(st, 32);
-    if (!active)
-        return;
-    C f[9], g[4], fo[9], go[4];
-    stage_pops<S, C>(st, lane, f, g);
+    using V = Vec<C, NV>;
+    // axial neighbours of rho u_r: the strip's columns form one sequence
+    // c = lane + 32 v; its ends read the staged halo, the lattice ends the
+    // boundary's ghost moments
+    V left, right;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+        const C up = __shfl_up_sync(0xffffffffu, mc.jr[c], 1);
+        const C dn = __shfl_down_sync(0xffffffffu, mc.jr[c], 1);
+        const C prev_last = __shfl_sync(0xffffffffu, mc.jr[(c + NV - 1) % NV], 31);
+        const C next_first = __shfl_sync(0xffffffffu, mc.jr[(c + 1) % NV], 0);
+        C l = up, r = dn;
+        if (lane == 0)
+            l = (c == 0) ? stage_jr<S, NV, C>(st, -1) : prev_last;
+        if (lane == 31)
+            r = (c == NV - 1) ? stage_jr<S, NV, C>(st, 32 * NV) : next_first;
+        const int i = x0 + lane + 32 * c;
+        if (i == 0)
+            l = jr_beyond_inlet<S, C>(p, src, j);
+        if (i == p.nx - 1)
+            r = jr_beyond_outlet<S, C>(p, src, j, mc.jr[c]);
+        left.set(c, l);
+        right.set(c, r);
+    }
+    if (x0 + lane >= p.nx)
+        return;  // no active node in this lane
+    V f[9], g[4], fo[9], go[4];
+    stage_pops<S, NV, C>(st, lane, f, g);
     const C inv_r = C(1) / (p.r0 + C(j) + C(0.5));
-    collide<C>(p, f, g, mc, inv_r, C(0.5) * (mn.jx - mp.jx), C(0.5) * (mn.jr - mp.jr), C(0.5) * (right - left),
-               C(0.5) * (mn.dT - mp.dT), fo, go);
-    S *o = dst + cell(p, 0, i, j);
+    collide<C, V>(p, f, g, mc, inv_r, C(0.5) * (mn.jx - mp.jx), C(0.5) * (mn.jr - mp.jr), C(0.5) * (right - left),
+                  C(0.5) * (mn.dT - mp.dT), fo, go);
+    const unsigned pl = (unsigned)p.plane;
 #pragma unroll
-    for (int k = 0; k < 9; ++k)
-        o[(int64_t)k * p.plane] = store_as<S, C>(fo[k]);
+    for (int c = 0; c < NV; ++c) {
+        const int i = x0 + lane + 32 * c;
+        if (i < p.nx) {
+            const unsigned o = (unsigned)((j + 1) * p.pitch + i + PAD_COLS);
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-        o[(int64_t)(9 + k) * p.plane] = store_as<S, C>(go[k]);
-    if (i == 0 || i == p.nx - 1 || j == 0 || j == p.nr - 1) {
-        C tf[9], tg[4];
+            for (int k = 0; k < 9; ++k)
+                dst[o + k * pl] = store_as<S, C>(fo[k][c]);
 #pragma unroll
-        for (int k = 0; k < 9; ++k)
-            tf[k] = fo[k];
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            tg[k] = go[k];
-        write_ghosts<S, C>(p, dst, i, j, tf, tg, p.step + 1);
+            for (int k = 0; k < 4; ++k)
+                dst[o + (9 + k) * pl] = store_as<S, C>(go[k][c]);
+            if (i == 0 || i == p.nx - 1 || j == 0 || j == p.nr - 1)
+                write_ghosts<S, C>(p, dst, i, j, p.step + 1);
+        }
     }
 }
 
-// One warp tile: columns x0..x0+31 of rows j0..j1-1.  Rows j0-1 (if any)
-// through min(j1, nr-1) are staged in order, NSTAGE - 2 rows ahead of the
-// one whose moments are being formed; row j is collided once the moments of
-// row j + 1 exist.
-template <class S, class C>
+// One warp tile: columns x0..x0+32 NV-1 of rows j0..j1-1.  Rows j0-1 (if
+// any) through min(j1, nr-1) are staged in order, NSTAGE - 2 rows ahead of
+// the one whose moments are being formed; row j is collided once the
+// moments of row j + 1 exist.  (The stage being refilled is never one of
+// the two being read: it held row idx - 2.)
+template <class S, int NV, class C>
 __device__ __forceinline__ void step_tile(const StepParams<C> &p, const S *__restrict__ src, S *__restrict__ dst,
                                           S *wsm, int tile, int lane)
 {
-    using Wn = Win<S>;
+    using Wn = Win<S, NV>;
+    using V = Vec<C, NV>;
+    constexpr int NSTAGE = Stages<NV>::value;
     constexpr int D = NSTAGE - 2;
     const int strip = tile % p.nstrips;
     const int band = tile / p.nstrips;
-    const int x0 = strip << 5;
+    const int x0 = strip * 32 * NV;
     const int j0 = band * p.band;
     const int j1 = min(j0 + p.band, p.nr);
     const int rfirst = j0 > 0 ? j0 - 1 : j0;
     const int nrows = min(j1, p.nr - 1) - rfirst + 1;
+    const CopyPlan<S, NV> plan = make_copy_plan<S, NV, C>(p, x0, lane);
 
 #pragma unroll
     for (int t = 0; t < D; ++t) {
         if (t < nrows)
-            issue_row<S, C>(p, src, wsm + t * Wn::STAGE, x0, rfirst + t, lane);
+            issue_row<S, NV, C>(p, src, wsm + t * Wn::STAGE, plan, rfirst + t, lane);
         cp_async_commit();
     }
-    Mom<C> mp, mc;
+    Mom<V> mp, mc;
 #pragma unroll 1
     for (int idx = 0; idx < nrows; ++idx) {
         __syncwarp();  // every lane is done with the stage refilled next
         if (idx + D < nrows)
-            issue_row<S, C>(p, src, wsm + ((idx + D) % NSTAGE) * Wn::STAGE, x0, rfirst + idx + D, lane);
+            issue_row<S, NV, C>(p, src, wsm + ((idx + D) % NSTAGE) * Wn::STAGE, plan, rfirst + idx + D, lane);
         cp_async_commit();
         cp_async_wait<D>();
         __syncwarp();  // row idx has landed for every lane
         const int r = rfirst + idx;
         const S *st = wsm + (idx % NSTAGE) * Wn::STAGE;
-        C f[9], g[4];
-        stage_pops<S, C>(st, lane, f, g);
-        const Mom<C> mr = moments<C>(f, g);
+        V f[9], g[4];
+        stage_pops<S, NV, C>(st, lane, f, g);
+        const Mom<V> mr = moments<V>(f, g);
         if (r < j0) {
             mp = mr;
         } else if (r == j0) {
             if (j0 == 0)
-                mp = ghost_bottom<C>(p, mr);
+                mp = ghost_bottom<C, V>(p, mr);
             mc = mr;
         } else {
-            collide_row<S, C>(p, src, dst, wsm + ((idx - 1) % NSTAGE) * Wn::STAGE, x0, lane, r - 1, mp, mc, mr);
+            collide_row<S, NV, C>(p, src, dst, wsm + ((idx - 1) % NSTAGE) * Wn::STAGE, x0, lane, r - 1, mp, mc, mr);
             mp = mc;
             mc = mr;
         }
     }
     if (j1 == p.nr)
-        collide_row<S, C>(p, src, dst, wsm + ((nrows - 1) % NSTAGE) * Wn::STAGE, x0, lane, p.nr - 1, mp, mc,
-                          ghost_top<C>(p, mc));
+        collide_row<S, NV, C>(p, src, dst, wsm + ((nrows - 1) % NSTAGE) * Wn::STAGE, x0, lane, p.nr - 1, mp, mc,
+                              ghost_top<C, V>(p, mc));
     cp_async_wait<0>();
     __syncwarp();
 }
 
-template <class S>
+template <class S, class C>
 constexpr int step_smem_per_warp()
 {
-    return NSTAGE * Win<S>::STAGE * (int)sizeof(S);
+    constexpr int NV = NodesPerLane<C>::value;
+    return Stages<NV>::value * Win<S, NV>::STAGE * (int)sizeof(S);
 }
 
 template <class S, class C>
 __global__ void __launch_bounds__(256) step_kernel(const __grid_constant__ StepParams<C> p)
 {
+    constexpr int NV = NodesPerLane<C>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -656,8 +795,8 @@ __global__ void __launch_bounds__(256) step_kernel(const __grid_constant__ StepP
     const int tile = blockIdx.x * wpc + warp;
     if (tile >= p.ntiles)
         return;  // whole warp
-    S *wsm = reinterpret_cast<S *>(smem_raw) + (size_t)warp * NSTAGE * Win<S>::STAGE;
-    step_tile<S, C>(p, static_cast<const S *>(p.src), static_cast<S *>(p.dst), wsm, tile, lane);
+    S *wsm = reinterpret_cast<S *>(smem_raw) + (size_t)warp * Stages<NV>::value * Win<S, NV>::STAGE;
+    step_tile<S, NV, C>(p, static_cast<const S *>(p.src), static_cast<S *>(p.dst), wsm, tile, lane);
 }
 
 // ---- ghosts of a stored state (after it is set from outside) ------------------------
@@ -670,15 +809,7 @@ __global__ void fill_ghosts_kernel(const __grid_constant__ StepParams<C> p)
     const int i = (int)(n % p.nx), j = (int)(n / p.nx);
     if (!(i == 0 || i == p.nx - 1 || j == 0 || j == p.nr - 1))
         return;
-    S *buf = static_cast<S *>(p.dst);
-    C tf[9], tg[4];
-#pragma unroll
-    for (int k = 0; k < 9; ++k)
-        tf[k] = load_as<S, C>(buf + cell(p, k, i, j));
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        tg[k] = load_as<S, C>(buf + cell(p, 9 + k, i, j));
-    write_ghosts<S, C>(p, buf, i, j, tf, tg, p.step);
+    write_ghosts<S, C>(p, static_cast<S *>(p.dst), i, j, p.step);
 }
 
 // ---- fields at the current time: Eq. 2 moments of the streamed populations ---------------
@@ -693,12 +824,19 @@ __global__ void fields_kernel(const __grid_constant__ StepParams<C> p, O *out)
     const S *src = static_cast<const S *>(p.src);
     C f[9], g[4];
     pull<S, C>(p, src, i, j, f, g);
-    const Mom<C> m = moments<C>(f, g);
-    const C rho = p.rho0 + m.drho;
+    Vec<C, 1> vf[9], vg[4];
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+        vf[k] = Vec<C, 1>(f[k]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        vg[k] = Vec<C, 1>(g[k]);
+    const Mom<Vec<C, 1>> m = moments<Vec<C, 1>>(vf, vg);
+    const C rho = p.rho0 + m.drho.x;
     out[n] = O(rho);
-    out[N + n] = O(m.jx / rho);
-    out[2 * N + n] = O(m.jr / rho);
-    out[3 * N + n] = O(p.T0 + m.dT);
+    out[N + n] = O(m.jx.x / rho);
+    out[2 * N + n] = O(m.jr.x / rho);
+    out[3 * N + n] = O(p.T0 + m.dT.x);
 }
 
 // ---- state conversion: absolute FP64 [q][j][i] <-> stored deviations -----------------

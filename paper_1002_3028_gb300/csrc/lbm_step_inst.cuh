@@ -11,7 +11,7 @@ cudaError_t LBM_CAT(launch_step_, LBM_TAG)(const StepParams<LBM_C> &p, int warps
 {
     if (p.ntiles <= 0)
         return cudaSuccess;
-    const int smem = warps_per_cta * step_smem_per_warp<LBM_S>();
+    const int smem = warps_per_cta * step_smem_per_warp<LBM_S, LBM_C>();
     step_kernel<LBM_S, LBM_C><<<ctas, 32 * warps_per_cta, smem, s>>>(p);
     return cudaGetLastError();
 }
@@ -21,11 +21,11 @@ cudaError_t LBM_CAT(launch_step_, LBM_TAG)(const StepParams<LBM_C> &p, int warps
 cudaError_t LBM_CAT(occupancy_step_, LBM_TAG)(int warps_per_cta, int *ctas_per_sm)
 {
     cudaError_t e = cudaFuncSetAttribute(step_kernel<LBM_S, LBM_C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         8 * step_smem_per_warp<LBM_S>());
+                                         8 * step_smem_per_warp<LBM_S, LBM_C>());
     if (e != cudaSuccess)
         return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, step_kernel<LBM_S, LBM_C>, 32 * warps_per_cta,
-                                                         warps_per_cta * step_smem_per_warp<LBM_S>());
+                                                         warps_per_cta * step_smem_per_warp<LBM_S, LBM_C>());
 }
 
 cudaError_t LBM_CAT(launch_fields_, LBM_TAG)(const StepParams<LBM_C> &p, void *out, int out_f64, cudaStream_t s)

@@ -46,7 +46,7 @@ def test_desc_struct_matches_header_layout(tmp_path):
 
 def test_required_bytes_counts_two_buffers():
     """Two buffers of 13 planes; each plane has ghost rows -1 and nr and a
-    padded row pitch (32 leading elements, columns 0..nx rounded up to 32,
+    padded row pitch (32 leading elements, columns 0..nx rounded up to 64,
     32 trailing elements)."""
     cfg = I.LatticeConfig(nx=100, nr=40)
     pitch = 32 + 128 + 32
