@@ -159,6 +159,13 @@ LBM_API int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream);
 /* Number of steps taken so far (the time index of the inlet noise). */
 LBM_API int64_t lbm_get_step(const lbm_lattice *h);
 
+/* Error flags raised on the device since the last call, then cleared:
+ * LBM_STATUS_TIMEOUT (1) = a bounded wait inside a kernel ran out (the
+ * steps since the last check are invalid).  0 = no error.  Synchronises the
+ * device. */
+#define LBM_STATUS_TIMEOUT 1
+LBM_API int lbm_check(lbm_lattice *h, int32_t *flags);
+
 /*
  * Macroscopic fields at the current time: the Eq. 2 moments rho, u_x, u_r,
  * T of the populations streamed from the stored state.  dev_out is caller
@@ -179,16 +186,49 @@ LBM_API int lbm_set_state(lbm_lattice *h, const double *dev_f, const double *dev
 
 /*
  * Launch shape of the step kernel: CTAs of warps_per_cta warps (1..8), one
- * warp per tile of 64 columns (32 for LBM_F64) x band_rows rows.  band_rows >= 1 fixes the
- * band height; 0 lets the library choose it from the number of warps the GPU
- * holds at once (the default).  warps_per_cta == 0 keeps the current value.
- * Results do not depend on the launch shape.
+ * warp per tile of 64 columns (32 for LBM_F64) x band_rows rows.
+ * band_rows >= 1 fixes the band height; 0 lets the library choose it from
+ * the number of warps the GPU holds at once (the default).
+ * warps_per_cta == 0 keeps the current value (default 2).  Results do not
+ * depend on the launch shape.
  */
 LBM_API int lbm_set_launch(lbm_lattice *h, int32_t band_rows, int32_t warps_per_cta);
 
 /* The launch shape lbm_step uses: band height, warps per CTA and CTAs per
  * launch (any pointer may be NULL). */
 LBM_API int lbm_get_launch(const lbm_lattice *h, int32_t *band_rows, int32_t *warps_per_cta, int32_t *ctas);
+
+/*
+ * Batches: independent lattices of any sizes (one storage type) stepped
+ * together, one launch per step over all members (every member advances
+ * exactly as it would alone under Eq. 1).
+ *   lbm_batch_create   empty batch for lattices of the given lbm_storage.
+ *   lbm_batch_add / lbm_batch_remove
+ *                      change the membership (takes effect at the next
+ *                      lbm_batch_step; a lattice belongs to one batch at a
+ *                      time; lbm_step on a member is an error; lbm_destroy
+ *                      removes it).  Members keep their own state, inlet,
+ *                      tables and step counter; lbm_get_fields and friends
+ *                      work on members as usual.
+ *   lbm_batch_step     nsteps steps of every member on the stream; with
+ *                      use_graph != 0, whole chunks of 16 steps are replayed
+ *                      from a captured CUDA graph (re-captured when the
+ *                      membership or a member's parameters change).
+ *   lbm_batch_set_launch / lbm_batch_get_launch
+ *                      launch shape shared by all members (as lbm_set_launch;
+ *                      tiles = warp tiles per step).
+ * The library allocates the batch's small device tables itself.  A batch
+ * and its members may be used from one host thread at a time.
+ */
+typedef struct lbm_batch lbm_batch;
+LBM_API int lbm_batch_create(int32_t storage, lbm_batch **out);
+LBM_API void lbm_batch_destroy(lbm_batch *b);
+LBM_API int lbm_batch_add(lbm_batch *b, lbm_lattice *h);
+LBM_API int lbm_batch_remove(lbm_batch *b, lbm_lattice *h);
+LBM_API int32_t lbm_batch_size(const lbm_batch *b);
+LBM_API int lbm_batch_step(lbm_batch *b, int32_t nsteps, int32_t use_graph, lbm_stream stream);
+LBM_API int lbm_batch_set_launch(lbm_batch *b, int32_t band_rows, int32_t warps_per_cta);
+LBM_API int lbm_batch_get_launch(const lbm_batch *b, int32_t *band_rows, int32_t *warps_per_cta, int32_t *tiles);
 
 #ifdef __cplusplus
 }

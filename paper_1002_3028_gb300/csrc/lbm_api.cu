@@ -65,6 +65,7 @@ struct Layout {
     size_t off_buf[2];
     size_t off_uin_d, off_tin_d, off_uin_f, off_tin_f;
     size_t off_nu_d, off_al_d, off_nu_f, off_al_f;
+    size_t off_status;
     size_t total;
 };
 
@@ -118,14 +119,18 @@ Layout make_layout(const lbm_desc *d)
     L.off_al_d = o; o += td;
     L.off_nu_f = o; o += tf;
     L.off_al_f = o; o += tf;
+    L.off_status = o; o += kAlign;
     L.total = o;
     return L;
 }
 
 }  // namespace
 
+struct lbm_batch;
+
 struct lbm_lattice {
     lbm_desc d;
+    lbm_batch *batch;  // the batch this lattice belongs to, if any
     Layout L;
     char *mem;
     bool own;
@@ -139,6 +144,23 @@ struct lbm_lattice {
 
     void *buf(int b) const { return mem + L.off_buf[b]; }
     template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(mem + off); }
+};
+
+struct lbm_batch {
+    int storage;
+    std::vector<lbm_lattice *> members;
+    bool dirty;      // membership or a member's parameters changed since the tables were built
+    int version;     // bumped on every rebuild (graph cache key)
+    void *d_params;  // StepParams<C>[members]
+    size_t cap_params;
+    lbm::TileRef *d_tiles;
+    size_t cap_tiles;
+    int ntiles;
+    int band, warps, band_eff;
+    int sms;
+    cudaStream_t capture;  // private stream used to capture step graphs
+    cudaGraphExec_t graph;
+    int graph_version, graph_steps;
 };
 
 namespace {
@@ -182,6 +204,7 @@ lbm::StepParams<C> make_params(const lbm_lattice *h, const C *u_in, const C *T_i
     p.T_in = T_in;
     p.nu_tab = nu;
     p.al_tab = al;
+    p.status = h->at<int>(h->L.off_status);
     return p;
 }
 
@@ -197,11 +220,11 @@ lbm::StepParams<float> params_f(const lbm_lattice *h)
                               h->at<float>(h->L.off_nu_f), h->at<float>(h->L.off_al_f));
 }
 
-// Launch shape of the step kernel: one warp per strip x band-row tile,
-// all tiles in one grid.  The automatic band height keeps about eight tiles
-// per resident warp (so CTAs start and finish at staggered times and the
-// last wave is short), bounded to 4..16 rows (each band pulls two extra
-// halo rows).
+// Launch shape of the step kernel: one warp per strip x band-row tile, all
+// tiles in one grid.  The automatic band height keeps about eight tiles per
+// resident warp (so CTAs start and finish at staggered times and the last
+// wave is short), bounded to 4..16 rows (each band pulls two extra halo
+// rows).
 int plan_launch(lbm_lattice *h)
 {
     int per_sm = 0;
@@ -226,7 +249,10 @@ int plan_launch(lbm_lattice *h)
         h->band_eff = (int)std::min<int64_t>(16, std::max<int64_t>(4, band));
     }
     const int64_t ntiles = (int64_t)nstrips * ((h->d.nr + h->band_eff - 1) / h->band_eff);
-    h->ctas = (int)((ntiles + h->warps - 1) / h->warps);
+    const int64_t ctas = (ntiles + h->warps - 1) / h->warps;
+    if (ctas > INT32_MAX)
+        return fail(LBM_ERR_INVALID_ARG, "too many tiles");
+    h->ctas = (int)ctas;
     return LBM_OK;
 }
 
@@ -285,6 +311,169 @@ bool valid(const lbm_lattice *h) { return h != nullptr && h->mem != nullptr; }
 
 }  // namespace
 
+
+// ---- batches ------------------------------------------------------------------------
+namespace {
+
+constexpr int kGraphSteps = 16;  // steps per captured graph of a batch
+
+size_t params_size(int storage)
+{
+    return storage == LBM_F64 ? sizeof(lbm::StepParams<double>) : sizeof(lbm::StepParams<float>);
+}
+
+int batch_occupancy(lbm_batch *b, int warps, int *per_sm)
+{
+    cudaError_t e;
+    switch (b->storage) {
+    case LBM_F64: e = lbm::occupancy_batch_f64(warps, per_sm); break;
+    case LBM_F32: e = lbm::occupancy_batch_f32(warps, per_sm); break;
+    case LBM_F16: e = lbm::occupancy_batch_f16(warps, per_sm); break;
+    default: e = lbm::occupancy_batch_bf16(warps, per_sm); break;
+    }
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "batch occupancy query");
+}
+
+void drop_graph(lbm_batch *b)
+{
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+}
+
+// build the parameter and tile tables of the current members
+int batch_rebuild(lbm_batch *b, cudaStream_t s)
+{
+    const int n = (int)b->members.size();
+    int per_sm = 0;
+    int rc = batch_occupancy(b, b->warps, &per_sm);
+    if (rc)
+        return rc;
+    if (per_sm < 1)
+        return fail(LBM_ERR_INVALID_ARG, "a CTA of %d warps does not fit on an SM", b->warps);
+    const int cols = strip_cols(b->storage);
+    int64_t area = 0;  // strips x rows over all members
+    for (lbm_lattice *h : b->members)
+        area += (int64_t)((h->d.nx + cols - 1) / cols) * h->d.nr;
+    if (b->band > 0) {
+        b->band_eff = b->band;
+    } else {
+        const int64_t want_tiles = 8 * (int64_t)per_sm * std::max(1, b->sms) * b->warps;
+        const int64_t band = (area + want_tiles - 1) / std::max<int64_t>(1, want_tiles);
+        b->band_eff = (int)std::min<int64_t>(16, std::max<int64_t>(4, band));
+    }
+    std::vector<lbm::TileRef> tiles;
+    std::vector<unsigned char> params(params_size(b->storage) * (size_t)std::max(1, n));
+    for (int m = 0; m < n; ++m) {
+        lbm_lattice *h = b->members[(size_t)m];
+        const int saved = h->band_eff;
+        h->band_eff = b->band_eff;
+        if (b->storage == LBM_F64) {
+            const auto p = params_d(h);
+            std::memcpy(params.data() + (size_t)m * sizeof(p), &p, sizeof(p));
+            for (int t = 0; t < p.ntiles; ++t)
+                tiles.push_back({m, t});
+        } else {
+            const auto p = params_f(h);
+            std::memcpy(params.data() + (size_t)m * sizeof(p), &p, sizeof(p));
+            for (int t = 0; t < p.ntiles; ++t)
+                tiles.push_back({m, t});
+        }
+        h->band_eff = saved;
+    }
+    if (tiles.size() > (size_t)INT32_MAX)
+        return fail(LBM_ERR_INVALID_ARG, "too many tiles in the batch");
+    cudaError_t e = cudaSuccess;
+    if (params.size() > b->cap_params || tiles.size() > b->cap_tiles) {
+        drop_graph(b);
+        cudaStreamSynchronize(s);  // the old tables may still be read by queued steps
+        if (params.size() > b->cap_params) {
+            cudaFree(b->d_params);
+            b->d_params = nullptr;
+            e = cudaMalloc(&b->d_params, params.size() * 2);
+            b->cap_params = e == cudaSuccess ? params.size() * 2 : 0;
+        }
+        if (e == cudaSuccess && tiles.size() > b->cap_tiles) {
+            cudaFree(b->d_tiles);
+            b->d_tiles = nullptr;
+            e = cudaMalloc(&b->d_tiles, std::max<size_t>(1, tiles.size() * 2) * sizeof(lbm::TileRef));
+            b->cap_tiles = e == cudaSuccess ? tiles.size() * 2 : 0;
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LBM_ERR_OOM, "batch table allocation: %s", cudaGetErrorString(e));
+        }
+    }
+    if (n > 0)
+        e = cudaMemcpyAsync(b->d_params, params.data(), params_size(b->storage) * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !tiles.empty())
+        e = cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(lbm::TileRef), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "batch table upload");
+    b->ntiles = (int)tiles.size();
+    b->dirty = false;
+    b->version += 1;
+    return LBM_OK;
+}
+
+cudaError_t batch_launch(lbm_batch *b, cudaStream_t s)
+{
+    const int n = (int)b->members.size();
+    switch (b->storage) {
+    case LBM_F64:
+        return lbm::launch_batch_f64(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<double> *>(b->d_params), n,
+                                     b->warps, s);
+    case LBM_F32:
+        return lbm::launch_batch_f32(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params), n,
+                                     b->warps, s);
+    case LBM_F16:
+        return lbm::launch_batch_f16(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params), n,
+                                     b->warps, s);
+    default:
+        return lbm::launch_batch_bf16(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params), n,
+                                      b->warps, s);
+    }
+}
+
+// instantiate (once per table version) a graph of kGraphSteps batch steps
+int batch_graph(lbm_batch *b)
+{
+    if (b->graph && b->graph_version == b->version)
+        return LBM_OK;
+    drop_graph(b);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+    for (int k = 0; e == cudaSuccess && k < kGraphSteps; ++k)
+        e = batch_launch(b, b->capture);
+    cudaError_t e2 = cudaStreamEndCapture(b->capture, &g);
+    if (e == cudaSuccess)
+        e = e2;
+    if (e == cudaSuccess)
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g)
+        cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph = nullptr;
+        cudaGetLastError();
+        return cuda_fail(e, "capturing the batch step graph");
+    }
+    b->graph_version = b->version;
+    b->graph_steps = kGraphSteps;
+    return LBM_OK;
+}
+
+void batch_advance_host(lbm_batch *b, int nsteps)
+{
+    for (lbm_lattice *h : b->members) {
+        h->step += nsteps;
+        if (nsteps & 1)
+            h->cur = 1 - h->cur;
+    }
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *lbm_last_error(void) { return g_err; }
@@ -318,6 +507,7 @@ int lbm_create(const lbm_desc *d, void *dev_mem, size_t bytes, lbm_lattice **out
         return fail(LBM_ERR_OOM, "host allocation failed");
     h->d = *d;
     h->L = L;
+    h->batch = nullptr;
     h->own = dev_mem == nullptr;
     h->cur = 0;
     h->step = 0;
@@ -381,6 +571,8 @@ void lbm_destroy(lbm_lattice *h)
 {
     if (!h)
         return;
+    if (h->batch)
+        lbm_batch_remove(h->batch, h);
     if (h->own && h->mem) {
         cudaDeviceSynchronize();
         cudaFree(h->mem);
@@ -404,6 +596,8 @@ int lbm_set_inlet(lbm_lattice *h, const double *u_in, const double *T_in, int32_
         rc = upload_pair(h, h->L.off_tin_d, h->L.off_tin_f, T_in, nr, s, "inlet upload");
     if (!rc)
         rc = fill_ghosts(h, s);  // the inlet ghosts carry the profile
+    if (h->batch)
+        h->batch->dirty = true;
     return rc;
 }
 
@@ -428,6 +622,8 @@ int lbm_set_properties(lbm_lattice *h, const double *nu, const double *alpha, in
     h->ntab = n;
     h->T_lo = T_lo;
     h->T_hi = n > 1 ? T_hi : T_lo + 1.0;
+    if (h->batch)
+        h->batch->dirty = true;
     return LBM_OK;
 }
 
@@ -435,6 +631,8 @@ int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
 {
     if (!valid(h) || nsteps < 0)
         return fail(LBM_ERR_INVALID_ARG, "bad handle or negative step count");
+    if (h->batch)
+        return fail(LBM_ERR_INVALID_ARG, "the lattice belongs to a batch: step the batch");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     for (int n = 0; n < nsteps; ++n) {
         cudaError_t e;
@@ -453,6 +651,20 @@ int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
 }
 
 int64_t lbm_get_step(const lbm_lattice *h) { return valid(h) ? h->step : -1; }
+
+int lbm_check(lbm_lattice *h, int32_t *flags)
+{
+    if (!valid(h) || !flags)
+        return fail(LBM_ERR_INVALID_ARG, "bad handle or NULL flags");
+    int v = 0;
+    cudaError_t e = cudaMemcpy(&v, h->mem + h->L.off_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemset(h->mem + h->L.off_status, 0, sizeof(int));
+    if (e != cudaSuccess)
+        return cuda_fail(e, "reading the status word");
+    *flags = v;
+    return LBM_OK;
+}
 
 int lbm_get_fields(lbm_lattice *h, void *dev_out, int32_t out_type, lbm_stream stream)
 {
@@ -506,6 +718,8 @@ int lbm_set_state(lbm_lattice *h, const double *dev_f, const double *dev_g, int6
     if (e != cudaSuccess)
         return cuda_fail(e, "state write kernel launch");
     h->step = step;
+    if (h->batch)
+        h->batch->dirty = true;
     return fill_ghosts(h, s);
 }
 
@@ -529,6 +743,134 @@ int lbm_get_launch(const lbm_lattice *h, int32_t *band_rows, int32_t *warps_per_
         *warps_per_cta = h->warps;
     if (ctas)
         *ctas = h->ctas;
+    return LBM_OK;
+}
+
+
+int lbm_batch_create(int32_t storage, lbm_batch **out)
+{
+    if (!out || storage_bytes(storage) == 0)
+        return fail(LBM_ERR_INVALID_ARG, "bad storage type or NULL out");
+    lbm_batch *b = new (std::nothrow) lbm_batch();
+    if (!b)
+        return fail(LBM_ERR_OOM, "host allocation failed");
+    b->storage = storage;
+    b->dirty = true;
+    b->warps = 2;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    b->sms = 1;
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "creating the capture stream");
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch *b)
+{
+    if (!b)
+        return;
+    cudaDeviceSynchronize();
+    for (lbm_lattice *h : b->members)
+        h->batch = nullptr;
+    drop_graph(b);
+    cudaFree(b->d_params);
+    cudaFree(b->d_tiles);
+    cudaStreamDestroy(b->capture);
+    delete b;
+}
+
+int lbm_batch_add(lbm_batch *b, lbm_lattice *h)
+{
+    if (!b || !valid(h))
+        return fail(LBM_ERR_INVALID_ARG, "bad batch or lattice handle");
+    if (h->batch)
+        return fail(LBM_ERR_INVALID_ARG, "the lattice already belongs to a batch");
+    if (h->d.storage != b->storage)
+        return fail(LBM_ERR_INVALID_ARG, "storage type %d differs from the batch's %d", h->d.storage, b->storage);
+    b->members.push_back(h);
+    h->batch = b;
+    b->dirty = true;
+    return LBM_OK;
+}
+
+int lbm_batch_remove(lbm_batch *b, lbm_lattice *h)
+{
+    if (!b || !h || h->batch != b)
+        return fail(LBM_ERR_INVALID_ARG, "the lattice is not in this batch");
+    for (size_t m = 0; m < b->members.size(); ++m)
+        if (b->members[m] == h) {
+            b->members.erase(b->members.begin() + (long)m);
+            break;
+        }
+    h->batch = nullptr;
+    b->dirty = true;
+    return LBM_OK;
+}
+
+int32_t lbm_batch_size(const lbm_batch *b) { return b ? (int32_t)b->members.size() : -1; }
+
+int lbm_batch_set_launch(lbm_batch *b, int32_t band_rows, int32_t warps_per_cta)
+{
+    if (!b || band_rows < 0 || warps_per_cta < 0 || warps_per_cta > 8)
+        return fail(LBM_ERR_INVALID_ARG, "bad batch or launch shape (warps per CTA 1..8)");
+    b->band = band_rows;
+    if (warps_per_cta > 0)
+        b->warps = warps_per_cta;
+    b->dirty = true;
+    return LBM_OK;
+}
+
+int lbm_batch_get_launch(const lbm_batch *b, int32_t *band_rows, int32_t *warps_per_cta, int32_t *tiles)
+{
+    if (!b)
+        return fail(LBM_ERR_INVALID_ARG, "bad batch handle");
+    if (band_rows)
+        *band_rows = b->band_eff;
+    if (warps_per_cta)
+        *warps_per_cta = b->warps;
+    if (tiles)
+        *tiles = b->ntiles;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch *b, int32_t nsteps, int32_t use_graph, lbm_stream stream)
+{
+    if (!b || nsteps < 0)
+        return fail(LBM_ERR_INVALID_ARG, "bad batch handle or negative step count");
+    if (b->members.empty() || nsteps == 0)
+        return LBM_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (b->dirty) {
+        int rc = batch_rebuild(b, s);
+        if (rc)
+            return rc;
+    }
+    int done = 0;
+    if (use_graph && nsteps >= kGraphSteps) {
+        int rc = batch_graph(b);
+        if (rc)
+            return rc;
+        for (; done + b->graph_steps <= nsteps; done += b->graph_steps) {
+            cudaError_t e = cudaGraphLaunch(b->graph, s);
+            if (e != cudaSuccess) {
+                batch_advance_host(b, done);
+                return cuda_fail(e, "batch graph launch");
+            }
+        }
+    }
+    for (; done < nsteps; ++done) {
+        cudaError_t e = batch_launch(b, s);
+        if (e != cudaSuccess) {
+            batch_advance_host(b, done);
+            return cuda_fail(e, "batch step launch");
+        }
+    }
+    batch_advance_host(b, nsteps);
     return LBM_OK;
 }
 

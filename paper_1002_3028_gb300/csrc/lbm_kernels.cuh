@@ -61,8 +61,9 @@ template <class C> struct NodesPerLane { static constexpr int value = 1; };
 template <> struct NodesPerLane<float> { static constexpr int value = 2; };
 
 // ---- kernel parameters -------------------------------------------------------
+// (16-byte aligned so a warp can copy a block from a batch table in 16-byte words)
 template <class C>
-struct StepParams {
+struct alignas(16) StepParams {
     const void *src;  // post-collision state of the previous step (with its ghosts)
     void *dst;        // post-collision state written by this step (with its ghosts)
     int64_t plane;    // elements per population plane ((nr + 2) * pitch)
@@ -82,6 +83,7 @@ struct StepParams {
     C T_lo, tab_scale;            // table position s = (T - T_lo) * tab_scale
     const C *u_in, *T_in;         // inlet profiles, nr values
     const C *nu_tab, *al_tab;     // property tables, ntab values
+    int *status;                  // error flags of the lattice
 };
 
 // ---- storage conversions -----------------------------------------------------
@@ -797,6 +799,63 @@ __global__ void __launch_bounds__(256) step_kernel(const __grid_constant__ StepP
         return;  // whole warp
     S *wsm = reinterpret_cast<S *>(smem_raw) + (size_t)warp * Stages<NV>::value * Win<S, NV>::STAGE;
     step_tile<S, NV, C>(p, static_cast<const S *>(p.src), static_cast<S *>(p.dst), wsm, tile, lane);
+}
+
+// ---- many lattices in one launch --------------------------------------------------------
+// A batch of independent lattices of any sizes (same storage type) steps in
+// one launch: a table lists every warp tile as (lattice, tile of that
+// lattice); each warp copies its lattice's parameters from the batch's
+// parameter table into shared memory and runs the same tile code.  The
+// parameters (buffers, step counter) advance on the device after each step
+// (advance_kernel), so a captured sequence of steps can be replayed.
+struct TileRef {
+    int lattice;  // index in the batch's parameter table
+    int tile;     // warp tile index within that lattice
+};
+
+template <class S, class C>
+__global__ void __launch_bounds__(256) batch_step_kernel(const TileRef *__restrict__ tiles, int ntiles,
+                                                         const StepParams<C> *__restrict__ lattices)
+{
+    constexpr int NV = NodesPerLane<C>::value;
+    constexpr int PW = (int)((sizeof(StepParams<C>) + 15) / 16);  // 16-byte words per parameter block
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpc = blockDim.x >> 5;
+    const int idx = blockIdx.x * wpc + warp;
+    if (idx >= ntiles)
+        return;  // whole warp
+    const TileRef t = tiles[idx];
+    // parameter blocks of all warps first, then the warps' staging rings
+    StepParams<C> *pw = reinterpret_cast<StepParams<C> *>(smem_raw) + warp;
+    static_assert(sizeof(StepParams<C>) % 16 == 0 && PW <= 32, "parameter block copy");
+    if (lane < PW)
+        reinterpret_cast<uint4 *>(pw)[lane] = reinterpret_cast<const uint4 *>(lattices + t.lattice)[lane];
+    __syncwarp();
+    const StepParams<C> &p = *pw;
+    S *wsm = reinterpret_cast<S *>(smem_raw + wpc * sizeof(StepParams<C>)) + (size_t)warp * Stages<NV>::value * Win<S, NV>::STAGE;
+    step_tile<S, NV, C>(p, static_cast<const S *>(p.src), static_cast<S *>(p.dst), wsm, t.tile, lane);
+}
+
+template <class S, class C>
+constexpr int batch_smem_per_warp()
+{
+    return step_smem_per_warp<S, C>() + (int)sizeof(StepParams<C>);
+}
+
+// after a batch step: every lattice swaps its buffers and counts the step
+template <class C>
+__global__ void advance_kernel(StepParams<C> *lattices, int n)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n)
+        return;
+    StepParams<C> &p = lattices[m];
+    const void *s = p.src;
+    p.src = p.dst;
+    p.dst = const_cast<void *>(s);
+    p.step += 1;
 }
 
 // ---- ghosts of a stored state (after it is set from outside) ------------------------

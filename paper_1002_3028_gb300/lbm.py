@@ -94,9 +94,22 @@ def lib(build: bool = True):
             L.lbm_set_state.argtypes = [vp, vp, vp, i64, vp]
             L.lbm_set_launch.argtypes = [vp, i32, i32]
             L.lbm_get_launch.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+            L.lbm_check.argtypes = [vp, C.POINTER(i32)]
+            L.lbm_batch_create.argtypes = [i32, C.POINTER(vp)]
+            L.lbm_batch_destroy.restype = None
+            L.lbm_batch_destroy.argtypes = [vp]
+            L.lbm_batch_add.argtypes = [vp, vp]
+            L.lbm_batch_remove.argtypes = [vp, vp]
+            L.lbm_batch_size.restype = i32
+            L.lbm_batch_size.argtypes = [vp]
+            L.lbm_batch_step.argtypes = [vp, i32, i32, vp]
+            L.lbm_batch_set_launch.argtypes = [vp, i32, i32]
+            L.lbm_batch_get_launch.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
             for name in ("lbm_required_bytes", "lbm_create", "lbm_set_inlet", "lbm_set_properties",
                          "lbm_step", "lbm_get_fields", "lbm_get_state", "lbm_set_state",
-                         "lbm_set_launch", "lbm_get_launch"):
+                         "lbm_set_launch", "lbm_get_launch", "lbm_check", "lbm_batch_create",
+                         "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_set_launch",
+                         "lbm_batch_get_launch"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -197,6 +210,12 @@ class Lattice:
     def step(self, n: int = 1, stream=None):
         _check(self._L.lbm_step(self._h, int(n), _stream_ptr(stream)), "lbm_step")
 
+    def check(self) -> int:
+        """Device error flags since the last check (0 = none); synchronises."""
+        v = C.c_int32()
+        _check(self._L.lbm_check(self._h, C.byref(v)), "lbm_check")
+        return v.value
+
     @property
     def step_count(self) -> int:
         return int(self._L.lbm_get_step(self._h))
@@ -236,3 +255,52 @@ class Lattice:
                                      int(step), _stream_ptr(stream)), "lbm_set_state")
         # keep the inputs alive until the conversion kernel has run
         torch.cuda.current_stream(self.device).synchronize() if stream is None else stream.synchronize()
+
+
+class Batch:
+    """Independent lattices of one storage type stepped together, one launch per step."""
+
+    def __init__(self, storage: str = "f16"):
+        if storage not in STORAGE:
+            raise ValueError(f"storage must be one of {sorted(STORAGE)}")
+        self.storage = storage
+        self._L = lib()
+        h = C.c_void_p()
+        _check(self._L.lbm_batch_create(STORAGE[storage], C.byref(h)), "lbm_batch_create")
+        self._h = h
+        self.members = []
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.lbm_batch_destroy(self._h)
+            self._h = None
+            self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return int(self._L.lbm_batch_size(self._h))
+
+    def add(self, lat: "Lattice"):
+        _check(self._L.lbm_batch_add(self._h, lat.handle), "lbm_batch_add")
+        self.members.append(lat)
+
+    def remove(self, lat: "Lattice"):
+        _check(self._L.lbm_batch_remove(self._h, lat.handle), "lbm_batch_remove")
+        self.members = [m for m in self.members if m is not lat]
+
+    def step(self, n: int = 1, graph: bool = True, stream=None):
+        _check(self._L.lbm_batch_step(self._h, int(n), int(bool(graph)), _stream_ptr(stream)), "lbm_batch_step")
+
+    def set_launch(self, band_rows: int = 0, warps_per_cta: int = 0):
+        _check(self._L.lbm_batch_set_launch(self._h, band_rows, warps_per_cta), "lbm_batch_set_launch")
+
+    def launch(self):
+        """(band rows, warps per CTA, warp tiles per step) of the last rebuilt tables."""
+        b, w, t = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(self._L.lbm_batch_get_launch(self._h, C.byref(b), C.byref(w), C.byref(t)), "lbm_batch_get_launch")
+        return b.value, w.value, t.value

@@ -13,7 +13,7 @@ def test_header_declares_the_boundary_calls():
     names = lbm.declared_symbols()
     for n in ("lbm_create", "lbm_set_inlet", "lbm_set_properties", "lbm_step", "lbm_get_fields",
               "lbm_destroy", "lbm_get_state", "lbm_set_state", "lbm_required_bytes",
-              "lbm_last_error", "lbm_get_step", "lbm_set_launch", "lbm_get_launch"):
+              "lbm_last_error", "lbm_get_step", "lbm_set_launch", "lbm_get_launch", "lbm_check"):
         assert n in names
 
 
