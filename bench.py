@@ -5,7 +5,8 @@ u = 0.08 (1 - (r/R)^2), T ratio 10, Smagorinsky Cs = 0.17, 256-entry
 nu(T) table), FP32 population storage.  One "step" is one time step of the
 whole lattice (one fused kernel launch).  The two population buffers
 (436 MB in FP32) are larger than the 129 MB L2, so no flush is needed
-between steps.
+between steps.  ``--workload ensemble`` steps 256 ragged jets as one batch
+(one launch per step, CUDA-graph replay); ``--workload jetNXxNR`` any size.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on the host cores on the same workload instead.
@@ -34,15 +35,25 @@ METRIC = "MLUPS & HBM-roofline % (D2Q9+D2Q4 LES); serving p50/p99 latency vs pla
 KERNEL_SRC = os.path.join(ROOT, "paper_1002_3028_gb300", "csrc", "lbm_kernels.cuh")
 
 
-def workload_by_name(name: str):
+def workloads_by_name(name: str):
+    """The lattices of a named workload: one jet, the pipe, or the ragged ensemble."""
     from paper_1002_3028_gb300 import inputs as I
 
     m = re.fullmatch(r"jet(\d+)x(\d+)", name)
     if m:
-        return I.jet_workload(nx=int(m.group(1)), nr=int(m.group(2)))
+        return [I.jet_workload(nx=int(m.group(1)), nr=int(m.group(2)))]
     if name == "pipe":
-        return I.pipe_workload()
+        return [I.pipe_workload()]
+    m = re.fullmatch(r"ensemble(\d*)", name)
+    if m:
+        return I.ensemble_workloads(int(m.group(1) or 256), seed=7)
     raise SystemExit(f"unknown workload {name}")
+
+
+def workload_label(name: str, ws) -> str:
+    if len(ws) == 1:
+        return f"jet {ws[0].cfg.nx}x{ws[0].cfg.nr}" if name.startswith("jet") else name
+    return f"ensemble of {len(ws)} ragged jets ({sum(w.nodes for w in ws)} nodes)"
 
 
 def measured_peaks():
@@ -128,49 +139,74 @@ def dist_env():
     return ws, rank, local
 
 
-def cpu_baseline(w, budget_s: float):
-    """The FP64 oracle on the host cores, on a bounded sample of the same lattice."""
+def cpu_baseline(ws, budget_s: float, label: str):
+    """The FP64 oracle on the host cores, on a bounded sample of the same workload.
+
+    One lattice: as many whole time steps as fit in about budget_s.  An
+    ensemble: one timed step (after a warm-up step) of each lattice in turn
+    until about budget_s has passed.
+    """
     from oracle import oracle
 
     cores = os.cpu_count() or 1
-    o = oracle.Oracle.from_workload(w, nthreads=cores)
-    o.step(1)  # warm-up
-    t0 = time.perf_counter()
-    n = 0
-    while True:
+    if len(ws) == 1:
+        w = ws[0]
+        o = oracle.Oracle.from_workload(w, nthreads=cores)
         o.step(1)
-        n += 1
-        if time.perf_counter() - t0 >= budget_s:
+        t0 = time.perf_counter()
+        steps = 0
+        while True:
+            o.step(1)
+            steps += 1
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        dt = time.perf_counter() - t0
+        o.close()
+        return {"value": w.nodes * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                "sample": f"{steps} time steps of the {w.cfg.nx}x{w.cfg.nr} lattice (FP64, after 1 warm-up step)"}
+    total_nodes, total_s, used = 0, 0.0, 0
+    t_start = time.perf_counter()
+    for w in ws:
+        o = oracle.Oracle.from_workload(w, nthreads=cores)
+        o.step(1)
+        t1 = time.perf_counter()
+        o.step(1)
+        total_s += time.perf_counter() - t1
+        total_nodes += w.nodes
+        used += 1
+        o.close()
+        if time.perf_counter() - t_start >= budget_s:
             break
-    dt = time.perf_counter() - t0
-    o.close()
-    return {"value": w.nodes * n / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{n} time steps of the {w.cfg.nx}x{w.cfg.nr} lattice (FP64, after 1 warm-up step)"}
+    return {"value": total_nodes / total_s / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"one timed step (after a warm-up step) of each of the first {used} lattices of {label}"}
 
 
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    w = workload_by_name(args.workload)
+    ws = workloads_by_name(args.workload)
     from oracle import oracle
 
     cores = os.cpu_count() or 1
-    o = oracle.Oracle.from_workload(w, nthreads=cores)
+    orcs = [oracle.Oracle.from_workload(w, nthreads=cores) for w in ws]
     for _ in range(args.warmup):
-        o.step(1)
+        for o in orcs:
+            o.step(1)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        o.step(1)
+        for o in orcs:
+            o.step(1)
     dt = time.perf_counter() - t0
-    mlups = w.nodes * args.steps / dt / 1e6
+    nodes = sum(w.nodes for w in ws)
+    mlups = nodes * args.steps / dt / 1e6
     line = {
         "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": f"jet {w.cfg.nx}x{w.cfg.nr}", "storage": "f64 (oracle)"},
+        "data": "synthetic", "config": {"workload": workload_label(args.workload, ws), "storage": "f64 (oracle)"},
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} full time steps of the {w.cfg.nx}x{w.cfg.nr} lattice"},
+                         "sample": f"{args.steps} full time steps of {workload_label(args.workload, ws)}"},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -189,27 +225,41 @@ def run_gpu(args):
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
 
-    from paper_1002_3028_gb300 import lbm
+    from paper_1002_3028_gb300 import autotune, lbm
 
-    w = workload_by_name(args.workload)
-    lat = lbm.Lattice.from_workload(w, args.storage, device=device)
-    if args.band or args.warps:
-        lat.set_launch(max(args.band, 0), args.warps)
+    works = workloads_by_name(args.workload)
+    label = workload_label(args.workload, works)
+    lats = [lbm.Lattice.from_workload(w, args.storage, device=device) for w in works]
+    nodes = sum(w.nodes for w in works)
     stream = torch.cuda.current_stream(device)
+    if len(lats) == 1:
+        target = lats[0]
+        step = target.step
+    else:  # an ensemble: one batch, one launch per step, graph replay
+        target = lbm.Batch(args.storage)
+        for lat in lats:
+            target.add(lat)
+
+        def step(n, stream=None):
+            target.step(n, graph=True, stream=stream)
+    if args.autotune:  # outside the timed region; the lattices advance while tuning
+        autotune.tune(target)
+    elif args.band or args.warps:
+        target.set_launch(max(args.band, 0), args.warps)
 
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(device)
 
-    # warm-up, then the device-timed region: K launches bracketed by events on the launching stream
-    lat.step(args.warmup)
+    # warm-up, then the device-timed region: K steps bracketed by events on the launching stream
+    step(args.warmup)
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         ev0.record(stream)
-        lat.step(args.steps)
+        step(args.steps)
         ev1.record(stream)
         ev1.synchronize()
     barrier()
@@ -218,38 +268,40 @@ def run_gpu(args):
         t = torch.tensor([ms], device=device)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    nodes = w.nodes
     mlups = nodes * args.steps * ws / (ms * 1e-3) / 1e6
     per_launch_s = ms * 1e-3 / args.steps
     bpl = POPS * 2 * BYTES_PER_VALUE[args.storage]
     achieved = bpl * nodes / per_launch_s / 1e9
     peak, peak_kind = measured_peaks()
+    finite = all(bool(torch.isfinite(lat.fields(dtype=torch.float32)).all().item()) for lat in lats)
+    flags = max(lat.check() for lat in lats)
 
-    finite = bool(torch.isfinite(lat.fields(dtype=torch.float32)).all().item())
-
-    # end to end through the public API: the job's initial state from pinned host memory,
-    # K steps, the job's result fields back to pinned host memory, all inside the timed region
-    nx, nr = w.cfg.nx, w.cfg.nr
-    f_h = torch.empty((9, nr, nx), dtype=torch.float64).pin_memory()
-    g_h = torch.empty((4, nr, nx), dtype=torch.float64).pin_memory()
-    fd, gd = lat.get_state()
-    f_h.copy_(fd)
-    g_h.copy_(gd)
-    del fd, gd
-    out_h = torch.empty((4, nr, nx), dtype=torch.float32).pin_memory()
-    f_d = torch.empty_like(f_h, device=device)
-    g_d = torch.empty_like(g_h, device=device)
-    out_d = torch.empty((4, nr, nx), dtype=torch.float32, device=device)
+    # end to end through the public API: every lattice's initial state from pinned host
+    # memory, K steps, every lattice's fields back to pinned host memory, all timed
+    host_states, dev_states, outs = [], [], []
+    for lat in lats:
+        fd, gd = lat.get_state()
+        fh = torch.empty(fd.shape, dtype=torch.float64).pin_memory()
+        gh = torch.empty(gd.shape, dtype=torch.float64).pin_memory()
+        fh.copy_(fd)
+        gh.copy_(gd)
+        host_states.append((fh, gh))
+        dev_states.append((torch.empty_like(fd), torch.empty_like(gd)))
+        outs.append((torch.empty((4, lat.nr, lat.nx), dtype=torch.float32, device=device),
+                     torch.empty((4, lat.nr, lat.nx), dtype=torch.float32).pin_memory()))
+        del fd, gd
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    f_d.copy_(f_h, non_blocking=True)
-    g_d.copy_(g_h, non_blocking=True)
-    lat.set_state(f_d, g_d, lat.step_count, stream=stream)
-    lat.step(args.steps)
-    lat.fields(out=out_d)
-    out_h.copy_(out_d, non_blocking=True)
+    for lat, (fh, gh), (fd, gd) in zip(lats, host_states, dev_states):
+        fd.copy_(fh, non_blocking=True)
+        gd.copy_(gh, non_blocking=True)
+        lat.set_state(fd, gd, lat.step_count, stream=stream)
+    step(args.steps, stream=stream)
+    for lat, (od, oh) in zip(lats, outs):
+        lat.fields(out=od)
+        oh.copy_(od, non_blocking=True)
     e1.record(stream)
     e1.synchronize()
     barrier()
@@ -258,41 +310,89 @@ def run_gpu(args):
         t = torch.tensor([e2e_ms], device=device)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(t.item())
-    h2d = (f_h.numel() + g_h.numel()) * 8
-    d2h = out_h.numel() * 4
+    h2d = sum((fh.numel() + gh.numel()) * 8 for fh, gh in host_states)
+    d2h = sum(oh.numel() * 4 for _, oh in outs)
     e2e = {"value": nodes * args.steps * ws / (e2e_ms * 1e-3) / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-           "note": "initial state uploaded, K steps, fields downloaded; copies amortised over K"}
+           "note": "initial states uploaded, K steps, fields downloaded; copies amortised over K"}
 
     if rank != 0:
         return 0
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, args.cpu_seconds)
+        cpu = cpu_baseline(works, args.cpu_seconds, label)
     traffic = ncu_traffic(args.storage, args.workload)
+    launch = target.launch()
     line = {
         "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage != "f64" else "f64",
         "data": "synthetic",
-        "config": {"workload": f"jet {nx}x{nr}", "storage": args.storage, "nodes": nodes,
+        "config": {"workload": label, "storage": args.storage, "nodes": nodes, "lattices": len(lats),
                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2": "no flush: inputs larger than L2 (two population buffers of "
                          f"{2 * POPS * BYTES_PER_VALUE[args.storage] * nodes / 1e6:.0f} MB)",
                    "bytes_per_lup": bpl,
-                   "launch": dict(zip(("band_rows", "warps_per_cta", "ctas"), lat.launch()))},
+                   "launch": dict(zip(("band_rows", "warps_per_cta", "ctas" if len(lats) == 1 else "tiles"),
+                                      launch))},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (1 if len(lats) == 1 else 2),
         "clocks": clk.summary(),
         "fields_finite": finite,
+        "device_flags": flags,
     }
     print(json.dumps(line), flush=True)
-    lat.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_serving(args):
+    """Continuous-batching service (FP16 batch) against the plain FP32 one-at-a-time path."""
+    import torch
+
+    from paper_1002_3028_gb300 import inputs as I
+    from paper_1002_3028_gb300 import lbm
+    from paper_1002_3028_gb300.serve import GpuBatchEngine, serve, serve_plain
+
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    reqs = I.request_stream(count=args.requests, rate_per_s=args.rate, seed=11)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        batched = serve(reqs, GpuBatchEngine("f16"), args.budget_gb * 1e9, chunk=args.chunk, keep_fields=True)
+    torch.cuda.synchronize()
+    plain = serve_plain(reqs, "f32")
+    # error of the served FP16 fields against an FP64 run of the same request, on a sample
+    errs = []
+    for res in batched.results[:: max(1, len(reqs) // 4)][:4]:
+        w = reqs[res.rid].workload
+        ref = lbm.Lattice.from_workload(w, "f64")
+        ref.step(w.steps)
+        F = ref.fields().cpu().numpy()
+        G = res.fields.double().numpy()
+        speed = max(float(abs(F[1]).max()), float(abs(F[2]).max()))
+        errs.append({"rid": res.rid, "u": float(abs(G[1:3] - F[1:3]).max() / speed),
+                     "T": float(abs(G[3] - F[3]).max() / abs(F[3]).max())})
+        ref.close()
+    b, p_ = batched.summary(), plain.summary()
+    line = {
+        "metric": METRIC, "value": b["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": None, "warmup": 0,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16 storage, f32 math",
+        "data": "synthetic",
+        "config": {"workload": f"serving: {len(reqs)} Poisson requests at {args.rate}/s, jets drawn like the "
+                               f"ensemble, steps U{{1000..20000}}, seed 11", "budget_gb": args.budget_gb,
+                   "chunk_steps": args.chunk},
+        "serving": {"batched_f16": b, "plain_f32_one_at_a_time": p_,
+                    "mlups_ratio_batched_over_plain": b["mlups"] / p_["mlups"],
+                    "f16_error_vs_f64_sample": errs},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -308,11 +408,18 @@ def main(argv=None):
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="tune the launch shape before timing")
+    ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
+    ap.add_argument("--rate", type=float, default=40.0, help="serving: arrivals per second")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: device memory budget")
+    ap.add_argument("--chunk", type=int, default=256, help="serving: most steps per batch launch sequence")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_gpu(args)
 
 

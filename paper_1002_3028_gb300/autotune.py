@@ -1,0 +1,103 @@
+"""Autotuner of the step kernel's launch shape (band height x warps per CTA).
+
+Times each candidate shape on the live lattice or batch with CUDA events on
+its stream (after a warm-up), keeps the fastest, and remembers it in a small
+JSON cache keyed by the GPU name, the storage type and the lattice shape(s),
+so a later lattice of the same kind starts from the tuned shape.  Tuning
+steps the lattice: tune before setting the initial state, or save and
+restore it (``Lattice.get_state`` / ``set_state``).
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import threading
+from typing import Iterable, List, Optional, Sequence, Tuple
+
+from . import build as _build
+
+CACHE = os.path.join(_build.BUILD, "autotune.json")
+DEFAULT_CANDIDATES: Tuple[Tuple[int, int], ...] = (
+    (4, 1), (4, 2), (4, 4), (6, 2), (8, 1), (8, 2), (8, 4), (12, 2), (16, 2), (16, 4),
+)
+_lock = threading.Lock()
+
+
+def _gpu_name() -> str:
+    import torch
+
+    return torch.cuda.get_device_name(torch.cuda.current_device())
+
+
+def _load() -> dict:
+    try:
+        with open(CACHE) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(key: str, value) -> None:
+    with _lock:
+        data = _load()
+        data[key] = value
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        tmp = CACHE + f".tmp{os.getpid()}"
+        with open(tmp, "w") as fh:
+            json.dump(data, fh, indent=1, sort_keys=True)
+        os.replace(tmp, CACHE)
+
+
+def lattice_key(storage: str, shapes: Iterable[Tuple[int, int]]) -> str:
+    shapes = sorted(shapes)
+    digest = hashlib.sha1(repr(shapes).encode()).hexdigest()[:12]
+    return f"{_gpu_name()}|{storage}|{len(shapes)}|{digest}"
+
+
+def _time(step_fn, steps: int, warmup: int) -> float:
+    import torch
+
+    step_fn(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    step_fn(steps)
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def tune(target, candidates: Optional[Sequence[Tuple[int, int]]] = None, steps: int = 50, warmup: int = 5,
+         use_cache: bool = True) -> Tuple[int, int]:
+    """Pick and set the fastest (band rows, warps per CTA) for a Lattice or Batch.
+
+    Returns the chosen shape.  With use_cache, a shape tuned earlier for the
+    same GPU, storage and lattice shapes is applied without timing.
+    """
+    from .lbm import Batch
+
+    is_batch = isinstance(target, Batch)
+    shapes = [(m.nx, m.nr) for m in target.members] if is_batch else [(target.nx, target.nr)]
+    key = lattice_key(target.storage, shapes)
+    if use_cache:
+        hit = _load().get(key)
+        if hit:
+            target.set_launch(int(hit["band"]), int(hit["warps"]))
+            return int(hit["band"]), int(hit["warps"])
+    if is_batch:
+        def run(n):
+            target.step(n, graph=False)
+    else:
+        run = target.step
+    results: List[Tuple[float, int, int]] = []
+    for band, warps in (candidates or DEFAULT_CANDIDATES):
+        target.set_launch(band, warps)
+        results.append((_time(run, steps, warmup), band, warps))
+    results.sort()
+    ms, band, warps = results[0]
+    target.set_launch(band, warps)
+    _store(key, {"band": band, "warps": warps, "ms_per_step": ms,
+                 "timings": [[b, w, t] for t, b, w in results]})
+    return band, warps
