@@ -159,6 +159,26 @@ LBM_API int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream);
 /* Number of steps taken so far (the time index of the inlet noise). */
 LBM_API int64_t lbm_get_step(const lbm_lattice *h);
 
+/*
+ * Global FP64 diagnostics of the current state (moments of Eq. 2 of the
+ * streamed populations at every node): mass = Σ rho and heat = Σ T over the
+ * nodes, mass_axi = Σ r rho and heat_axi = Σ r T (the axisymmetric
+ * volume weight, 2 pi r dx dr up to the constant), max_speed = max |u|, the
+ * steady-state residual between the current and the previous step
+ * (residual_max = max |u(t) - u(t-1)| / max |u(t)|, residual_l2 =
+ * sqrt(Σ |u(t) - u(t-1)|^2 / Σ |u(t)|^2); NaN unless the last change of the
+ * state was a step), and nonfinite = the number of nodes whose density is
+ * not finite and positive or whose velocity or temperature is not finite.
+ * Uses the lattice's own scratch area; synchronises the stream and writes
+ * *out.  Returns LBM_ERR_DIVERGED (with *out filled) when nonfinite > 0.
+ */
+typedef struct {
+    double mass, mass_axi, heat, heat_axi;
+    double max_speed, residual_max, residual_l2;
+    int64_t nonfinite;
+} lbm_diag;
+LBM_API int lbm_diagnostics(lbm_lattice *h, lbm_diag *out, lbm_stream stream);
+
 /* Error flags raised on the device since the last call, then cleared:
  * LBM_STATUS_TIMEOUT (1) = a bounded wait inside a kernel ran out (the
  * steps since the last check are invalid).  0 = no error.  Synchronises the

@@ -66,6 +66,7 @@ struct Layout {
     size_t off_uin_d, off_tin_d, off_uin_f, off_tin_f;
     size_t off_nu_d, off_al_d, off_nu_f, off_al_f;
     size_t off_status;
+    size_t off_diag;  // diagnostics scratch: block partials, then the folded result
     size_t total;
 };
 
@@ -120,6 +121,7 @@ Layout make_layout(const lbm_desc *d)
     L.off_nu_f = o; o += tf;
     L.off_al_f = o; o += tf;
     L.off_status = o; o += kAlign;
+    L.off_diag = o; o += align_up((size_t)(lbm::DIAG_MAX_BLOCKS + 1) * lbm::DIAG_SLOTS * sizeof(double));
     L.total = o;
     return L;
 }
@@ -138,6 +140,7 @@ struct lbm_lattice {
     int64_t step;
     int ntab;
     double T_lo, T_hi;
+    bool prev_valid;       // the other buffer holds the state one step earlier
     int band, warps;       // launch shape; band 0 = chosen from the occupancy
     int band_eff, ctas;    // band and CTA count used by lbm_step
     int device, sms;
@@ -469,7 +472,27 @@ void batch_advance_host(lbm_batch *b, int nsteps)
         h->step += nsteps;
         if (nsteps & 1)
             h->cur = 1 - h->cur;
+        if (nsteps > 0)
+            h->prev_valid = true;
     }
+}
+
+// fill an lbm_diag from the folded FP64 slots of the diagnostics reduction
+int finish_diag(const double *v, int have_prev, lbm_diag *out)
+{
+    out->mass = v[0];
+    out->mass_axi = v[1];
+    out->heat = v[2];
+    out->heat_axi = v[3];
+    out->max_speed = v[6];
+    const double nan = std::nan("");
+    out->residual_l2 = (have_prev && v[8] > 0.0) ? std::sqrt(v[4] / v[8]) : nan;
+    out->residual_max = (have_prev && v[6] > 0.0) ? v[5] / v[6] : nan;
+    out->nonfinite = (int64_t)v[7];
+    if (out->nonfinite > 0)
+        return fail(LBM_ERR_DIVERGED, "%lld nodes with non-finite or non-positive density or temperature",
+                    (long long)out->nonfinite);
+    return LBM_OK;
 }
 
 }  // namespace
@@ -508,6 +531,7 @@ int lbm_create(const lbm_desc *d, void *dev_mem, size_t bytes, lbm_lattice **out
     h->d = *d;
     h->L = L;
     h->batch = nullptr;
+    h->prev_valid = false;
     h->own = dev_mem == nullptr;
     h->cur = 0;
     h->step = 0;
@@ -646,11 +670,40 @@ int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
             return cuda_fail(e, "step kernel launch");
         h->cur = 1 - h->cur;
         h->step += 1;
+        h->prev_valid = true;
     }
     return LBM_OK;
 }
 
 int64_t lbm_get_step(const lbm_lattice *h) { return valid(h) ? h->step : -1; }
+
+int lbm_diagnostics(lbm_lattice *h, lbm_diag *out, lbm_stream stream)
+{
+    if (!valid(h) || !out)
+        return fail(LBM_ERR_INVALID_ARG, "bad handle or NULL output");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t N = (int64_t)h->d.nx * h->d.nr;
+    const int nblocks = (int)std::min<int64_t>(
+        {(int64_t)lbm::DIAG_MAX_BLOCKS, (N + lbm::DIAG_THREADS - 1) / lbm::DIAG_THREADS, 4 * (int64_t)h->sms});
+    double *partials = h->at<double>(h->L.off_diag);
+    double *res = partials + (size_t)lbm::DIAG_MAX_BLOCKS * lbm::DIAG_SLOTS;
+    const int prev = h->prev_valid ? 1 : 0;
+    cudaError_t e;
+    switch (h->d.storage) {
+    case LBM_F64: e = lbm::launch_diag_f64(params_d(h), prev, partials, nblocks, res, s); break;
+    case LBM_F32: e = lbm::launch_diag_f32(params_f(h), prev, partials, nblocks, res, s); break;
+    case LBM_F16: e = lbm::launch_diag_f16(params_f(h), prev, partials, nblocks, res, s); break;
+    default: e = lbm::launch_diag_bf16(params_f(h), prev, partials, nblocks, res, s); break;
+    }
+    double v[lbm::DIAG_SLOTS];
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(v, res, sizeof(v), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "diagnostics");
+    return finish_diag(v, prev, out);
+}
 
 int lbm_check(lbm_lattice *h, int32_t *flags)
 {
@@ -718,6 +771,7 @@ int lbm_set_state(lbm_lattice *h, const double *dev_f, const double *dev_g, int6
     if (e != cudaSuccess)
         return cuda_fail(e, "state write kernel launch");
     h->step = step;
+    h->prev_valid = false;
     if (h->batch)
         h->batch->dirty = true;
     return fill_ghosts(h, s);

@@ -19,10 +19,14 @@ namespace lbm {
     cudaError_t occupancy_batch_##TAG(int warps_per_cta, int *ctas_per_sm);                            \
     cudaError_t launch_fields_##TAG(const StepParams<C> &p, void *out, int out_f64, cudaStream_t s);   \
     cudaError_t launch_fill_##TAG(const StepParams<C> &p, cudaStream_t s);                             \
+    cudaError_t launch_diag_##TAG(const StepParams<C> &p, int have_prev, double *partials, int nblocks,     \
+                                  double *out, cudaStream_t s);                                        \
     cudaError_t launch_state_in_##TAG(void *buf, const double *f, const double *g, int nx, int nr,     \
                                       int pitch, int64_t plane, double rho0, double T0, cudaStream_t s); \
     cudaError_t launch_state_out_##TAG(const void *buf, double *f, double *g, int nx, int nr, int pitch, \
                                        int64_t plane, double rho0, double T0, cudaStream_t s);
+
+constexpr int DIAG_MAX_BLOCKS = 1024;  // partial-sum blocks of the diagnostics reduction
 
 LBM_DECLARE_LAUNCHERS(f64, double)
 LBM_DECLARE_LAUNCHERS(f32, float)

@@ -898,6 +898,110 @@ __global__ void fields_kernel(const __grid_constant__ StepParams<C> p, O *out)
     out[3 * N + n] = O(p.T0 + m.dT.x);
 }
 
+// ---- FP64 diagnostics: mass, heat, steady residual, divergence -------------------------
+// Per node, from the populations streamed from the current state (and from
+// the previous state in the other buffer): rho, u, T of Eq. 2.  Sums run in
+// FP64: Σ rho, Σ r rho, Σ T, Σ r T, Σ |u(t) - u(t-1)|^2, Σ |u(t)|^2,
+// max |u(t) - u(t-1)|, max |u(t)|, and the count of nodes whose rho is not
+// finite and positive or whose T is not finite.  Block partials go to
+// `partials` (DIAG_SLOTS doubles per block); diag_final_kernel folds them.
+constexpr int DIAG_SLOTS = 9;
+constexpr int DIAG_THREADS = 256;
+
+__device__ __forceinline__ void diag_combine(double *a, const double *b)
+{
+    for (int k = 0; k < 5; ++k)
+        a[k] += b[k];
+    a[5] = fmax(a[5], b[5]);
+    a[6] = fmax(a[6], b[6]);
+    a[7] += b[7];
+    a[8] += b[8];
+}
+
+// block-wide combine of per-thread slots through shared memory; thread 0 ends with the result
+__device__ __forceinline__ void diag_block_reduce(double (&v)[DIAG_SLOTS])
+{
+    __shared__ double sh[DIAG_THREADS / 32][DIAG_SLOTS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int off = 16; off > 0; off >>= 1) {
+        double o[DIAG_SLOTS];
+        for (int k = 0; k < DIAG_SLOTS; ++k)
+            o[k] = __shfl_down_sync(0xffffffffu, v[k], off);
+        diag_combine(v, o);
+    }
+    if (lane == 0)
+        for (int k = 0; k < DIAG_SLOTS; ++k)
+            sh[warp][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            diag_combine(v, sh[w]);
+}
+
+template <class S, class C>
+__global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const __grid_constant__ StepParams<C> p, int have_prev,
+                                                            double *partials)
+{
+    double v[DIAG_SLOTS] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const int64_t N = (int64_t)p.nx * p.nr;
+    const S *cur = static_cast<const S *>(p.src);
+    const S *prev = static_cast<const S *>(p.dst);
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(n % p.nx), j = (int)(n / p.nx);
+        C f[9], g[4];
+        pull<S, C>(p, cur, i, j, f, g);
+        Vec<C, 1> vf[9], vg[4];
+        for (int k = 0; k < 9; ++k)
+            vf[k] = Vec<C, 1>(f[k]);
+        for (int k = 0; k < 4; ++k)
+            vg[k] = Vec<C, 1>(g[k]);
+        const Mom<Vec<C, 1>> m = moments<Vec<C, 1>>(vf, vg);
+        const double rho = (double)p.rho0 + (double)m.drho.x;
+        const double T = (double)p.T0 + (double)m.dT.x;
+        const double ux = (double)m.jx.x / rho, ur = (double)m.jr.x / rho;
+        const double r = (double)p.r0 + j + 0.5;
+        if (!(rho > 0.0) || !isfinite(rho) || !isfinite(T) || !isfinite(ux) || !isfinite(ur)) {
+            v[7] += 1.0;
+            continue;
+        }
+        v[0] += rho;
+        v[1] += r * rho;
+        v[2] += T;
+        v[3] += r * T;
+        const double uu = ux * ux + ur * ur;
+        v[8] += uu;
+        v[6] = fmax(v[6], sqrt(uu));
+        if (have_prev) {
+            pull<S, C>(p, prev, i, j, f, g);
+            for (int k = 0; k < 9; ++k)
+                vf[k] = Vec<C, 1>(f[k]);
+            for (int k = 0; k < 4; ++k)
+                vg[k] = Vec<C, 1>(g[k]);
+            const Mom<Vec<C, 1>> q = moments<Vec<C, 1>>(vf, vg);
+            const double rp = (double)p.rho0 + (double)q.drho.x;
+            const double dx = ux - (double)q.jx.x / rp, dr = ur - (double)q.jr.x / rp;
+            v[4] += dx * dx + dr * dr;
+            v[5] = fmax(v[5], sqrt(dx * dx + dr * dr));
+        }
+    }
+    diag_block_reduce(v);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < DIAG_SLOTS; ++k)
+            partials[(int64_t)blockIdx.x * DIAG_SLOTS + k] = v[k];
+}
+
+// one block folds nblocks partials into out[0 .. DIAG_SLOTS-1]
+static __global__ void __launch_bounds__(DIAG_THREADS) diag_final_kernel(const double *partials, int nblocks, double *out)
+{
+    double v[DIAG_SLOTS] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        diag_combine(v, partials + (int64_t)b * DIAG_SLOTS);
+    diag_block_reduce(v);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < DIAG_SLOTS; ++k)
+            out[k] = v[k];
+}
+
 // ---- state conversion: absolute FP64 [q][j][i] <-> stored deviations -----------------
 template <class S>
 using compute_t = typename std::conditional<std::is_same<S, double>::value, double, float>::type;

@@ -76,6 +76,18 @@ cudaError_t LBM_CAT(launch_fill_, LBM_TAG)(const StepParams<LBM_C> &p, cudaStrea
     return cudaGetLastError();
 }
 
+// FP64 diagnostics: nblocks partial sums into `partials`, folded into out[DIAG_SLOTS]
+cudaError_t LBM_CAT(launch_diag_, LBM_TAG)(const StepParams<LBM_C> &p, int have_prev, double *partials, int nblocks,
+                                           double *out, cudaStream_t s)
+{
+    diag_kernel<LBM_S, LBM_C><<<nblocks, DIAG_THREADS, 0, s>>>(p, have_prev, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    diag_final_kernel<<<1, DIAG_THREADS, 0, s>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+
 cudaError_t LBM_CAT(launch_state_in_, LBM_TAG)(void *buf, const double *f, const double *g, int nx, int nr, int pitch,
                                                int64_t plane, double rho0, double T0, cudaStream_t s)
 {

@@ -48,6 +48,17 @@ class Desc(C.Structure):
     ]
 
 
+class Diag(C.Structure):
+    """Mirror of ``lbm_diag``."""
+
+    _fields_ = [("mass", C.c_double), ("mass_axi", C.c_double), ("heat", C.c_double), ("heat_axi", C.c_double),
+                ("max_speed", C.c_double), ("residual_max", C.c_double), ("residual_l2", C.c_double),
+                ("nonfinite", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 def make_desc(cfg: LatticeConfig, storage: str) -> Desc:
     return Desc(nx=cfg.nx, nr=cfg.nr, storage=STORAGE[storage], bc_in=_BC_IN[cfg.bc_in],
                 bc_out=_BC_OUT[cfg.bc_out], bc_top=_BC_TOP[cfg.bc_top],
@@ -95,6 +106,7 @@ def lib(build: bool = True):
             L.lbm_set_launch.argtypes = [vp, i32, i32]
             L.lbm_get_launch.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
             L.lbm_check.argtypes = [vp, C.POINTER(i32)]
+            L.lbm_diagnostics.argtypes = [vp, C.POINTER(Diag), vp]
             L.lbm_batch_create.argtypes = [i32, C.POINTER(vp)]
             L.lbm_batch_destroy.restype = None
             L.lbm_batch_destroy.argtypes = [vp]
@@ -109,7 +121,7 @@ def lib(build: bool = True):
                          "lbm_step", "lbm_get_fields", "lbm_get_state", "lbm_set_state",
                          "lbm_set_launch", "lbm_get_launch", "lbm_check", "lbm_batch_create",
                          "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_set_launch",
-                         "lbm_batch_get_launch"):
+                         "lbm_batch_get_launch", "lbm_diagnostics"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -209,6 +221,20 @@ class Lattice:
 
     def step(self, n: int = 1, stream=None):
         _check(self._L.lbm_step(self._h, int(n), _stream_ptr(stream)), "lbm_step")
+
+    def diagnostics(self, stream=None) -> dict:
+        """FP64 mass, heat, max speed, steady residual and non-finite count (synchronises).
+
+        ``diverged`` is True when some node has a non-finite or non-positive
+        density or a non-finite velocity or temperature.
+        """
+        d = Diag()
+        rc = self._L.lbm_diagnostics(self._h, C.byref(d), _stream_ptr(stream))
+        if rc not in (LBM_OK, -4):
+            _check(rc, "lbm_diagnostics")
+        out = d.as_dict()
+        out["diverged"] = rc == -4
+        return out
 
     def check(self) -> int:
         """Device error flags since the last check (0 = none); synchronises."""
