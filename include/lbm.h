@@ -179,6 +179,28 @@ typedef struct {
 } lbm_diag;
 LBM_API int lbm_diagnostics(lbm_lattice *h, lbm_diag *out, lbm_stream stream);
 
+/*
+ * lbm_diagnostics_noalloc: the same diagnostics as lbm_diagnostics (same
+ * quantities, equal up to FP64 summation order), for callers that cannot
+ * allocate device memory: programs whose device memory is entirely handed
+ * out by another allocator or budget, or that must keep a fixed device
+ * footprint once set up.  It allocates nothing and does not use the
+ * lattice's scratch area: its partial sums go to one fixed array compiled
+ * into this library (1.2 MB, which every GPU that loads the library holds
+ * until the process exits).  The paper has no counterpart; it is a service
+ * of this library.
+ *   - Lattices of at most 16384 rows (nr); larger ones are refused with
+ *     LBM_ERR_INVALID_ARG (use lbm_diagnostics for them).
+ *   - The lattice's device must be current.  The first call on a device
+ *     looks up the array's device address (no allocation); make that first
+ *     call before any stream capture.
+ *   - Every call on a device shares the array and overwrites the slots it
+ *     uses (nothing needs to start at zero); calls whose work overlaps on
+ *     the GPU, from any thread or stream, race on it.
+ *   - Synchronises the stream; returns LBM_ERR_DIVERGED as lbm_diagnostics.
+ */
+LBM_API int lbm_diagnostics_noalloc(lbm_lattice *h, lbm_diag *out, lbm_stream stream);
+
 /* Error flags raised on the device since the last call, then cleared:
  * LBM_STATUS_TIMEOUT (1) = a bounded wait inside a kernel ran out (the
  * steps since the last check are invalid).  0 = no error.  Synchronises the

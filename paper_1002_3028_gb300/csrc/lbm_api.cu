@@ -497,6 +497,30 @@ int finish_diag(const double *v, int have_prev, lbm_diag *out)
 
 }  // namespace
 
+namespace lbm {
+
+int lattice_view(const lbm_lattice *h, LatticeView *out)
+{
+    if (!valid(h) || !out)
+        return fail(LBM_ERR_INVALID_ARG, "bad handle or NULL output");
+    out->storage = h->d.storage;
+    out->device = h->device;
+    out->prev_valid = h->prev_valid ? 1 : 0;
+    out->nx = h->d.nx;
+    out->nr = h->d.nr;
+    if (h->d.storage == LBM_F64)
+        out->pd = params_d(h);
+    else
+        out->pf = params_f(h);
+    return LBM_OK;
+}
+
+int api_fail(int code, const char *msg) { return fail(code, "%s", msg); }
+
+int diag_finish(const double *v, int have_prev, lbm_diag *out) { return finish_diag(v, have_prev, out); }
+
+}  // namespace lbm
+
 extern "C" {
 
 const char *lbm_last_error(void) { return g_err; }

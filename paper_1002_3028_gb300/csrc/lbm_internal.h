@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "lbm.h"
 #include "lbm_kernels.cuh"
 
 namespace lbm {
@@ -34,5 +35,17 @@ LBM_DECLARE_LAUNCHERS(f16, float)
 LBM_DECLARE_LAUNCHERS(bf16, float)
 
 #undef LBM_DECLARE_LAUNCHERS
+
+// Read-only view of a lattice handle for entry points defined outside
+// lbm_api.cu (parameters of both arithmetic types, current device, whether
+// the other buffer holds the previous step).
+struct LatticeView {
+    int storage, device, prev_valid, nx, nr;
+    StepParams<double> pd;
+    StepParams<float> pf;
+};
+int lattice_view(const lbm_lattice *h, LatticeView *out);
+int api_fail(int code, const char *msg);                       // sets lbm_last_error
+int diag_finish(const double *v, int have_prev, lbm_diag *out); // fills lbm_diag from folded slots
 
 }  // namespace lbm

@@ -107,6 +107,7 @@ def lib(build: bool = True):
             L.lbm_get_launch.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
             L.lbm_check.argtypes = [vp, C.POINTER(i32)]
             L.lbm_diagnostics.argtypes = [vp, C.POINTER(Diag), vp]
+            L.lbm_diagnostics_noalloc.argtypes = [vp, C.POINTER(Diag), vp]
             L.lbm_batch_create.argtypes = [i32, C.POINTER(vp)]
             L.lbm_batch_destroy.restype = None
             L.lbm_batch_destroy.argtypes = [vp]
@@ -121,7 +122,7 @@ def lib(build: bool = True):
                          "lbm_step", "lbm_get_fields", "lbm_get_state", "lbm_set_state",
                          "lbm_set_launch", "lbm_get_launch", "lbm_check", "lbm_batch_create",
                          "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_set_launch",
-                         "lbm_batch_get_launch", "lbm_diagnostics"):
+                         "lbm_batch_get_launch", "lbm_diagnostics", "lbm_diagnostics_noalloc"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
