@@ -37,25 +37,31 @@ class _Params(C.Structure):
     ]
 
 
+def compile_source(src: str, out: str) -> str:
+    """Compile an oracle source file with gcc (C99, OpenMP, no FMA contraction)."""
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c99", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-fvisibility=hidden", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (C99, OpenMP, no FMA contraction)."""
+    """Compile the oracle (once; again when the source is newer than the library)."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-std=c99", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-fvisibility=hidden", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    return compile_source(_SRC, _LIB_PATH)
 
 
 def lib():
+    """The oracle library; ORACLE_LIB names a prebuilt one (the mutation tests use it)."""
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
+            L = C.CDLL(os.environ.get("ORACLE_LIB") or build())
             dp = C.POINTER(C.c_double)
             L.orc_create.restype = C.c_void_p
             L.orc_create.argtypes = [C.POINTER(_Params)]

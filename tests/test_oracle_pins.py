@@ -231,6 +231,80 @@ def test_turbulent_prandtl_coupling(orc):
     assert diag[1] == pytest.approx(0.5 + 2 * (alpha + nu_t / 0.3), rel=1e-14)
 
 
+# ---- lattice derivatives feeding Eq. 1 ----------------------------------------
+
+def _polynomial_state(orc, nx, nr, case):
+    """Equilibrium populations whose streamed moments are polynomials of degree <= 2 in x and in r.
+
+    Case "radial": rho = 1, u_x = U, u_r = a r (1 + b x), T = T0 + c x.
+    Case "thermal": rho = 1 + e r^2, u_x = U (1 + b x), u_r = 0, T = T0 + c r^2.
+    Both extend across the axis as mirror images (rho, u_x, T even in r, u_r
+    odd), so the axis rows are polynomial too.
+    """
+    f = np.empty((9, nr, nx))
+    g = np.empty((4, nr, nx))
+    for j, r in enumerate(I.radii(nr)):
+        for i in range(nx):
+            if case == "radial":
+                rho, ux, ur, T = 1.0, 0.04, 2e-3 * r * (1 + 0.05 * i), 1.0 + 0.02 * i
+            else:
+                rho, ux, ur, T = 1.0 + 4e-4 * r * r, 0.03 * (1 + 0.05 * i), 0.0, 1.0 + 2e-3 * r * r
+            f[:, j, i] = orc.feq(rho, ux, ur)
+            g[:, j, i] = orc.geq(T, ux, ur)
+    return f, g
+
+
+@pytest.mark.parametrize("case", ["radial", "thermal"])
+def test_lattice_derivatives_are_exact_on_quadratics(orc, case):
+    """The gradients entering F2 and S are exact derivatives of the streamed moments.
+
+    A central difference is exact on a quadratic, so with streamed moments
+    that are polynomials of degree <= 2 the collision of every node away from
+    the wall and the periodic seam must equal the node collision given the
+    analytic derivatives (taken from a least-squares polynomial fit of the
+    streamed moments).  This pins the stencil, its 1/2, and the parities of
+    the moments at the axis.
+    """
+    nx, nr, nu, alpha, Cs = 12, 10, 0.1, 0.12, 0.17
+    cfg = I.LatticeConfig(nx=nx, nr=nr, bc_in="periodic", bc_out="periodic", bc_top="wall",
+                          bc_bottom="axis", axisym=True, Cs=Cs, T_top=1.0)
+    o = orc.Oracle(cfg)
+    o.set_properties(np.array([nu]), np.array([alpha]), 0.0, 2.0)
+    f, g = _polynomial_state(orc, nx, nr, case)
+    o.set_state(f, g)
+    fs, gs = o.streamed()
+    o.step(1)
+    f1, g1 = o.get_state()
+
+    e9 = np.array(E9, dtype=float)
+    mom = np.stack([fs.sum(0), np.einsum("k,kji->ji", e9[:, 0], fs), np.einsum("k,kji->ji", e9[:, 1], fs),
+                    gs.sum(0)])
+    P = np.polynomial.polynomial
+    cols = np.arange(1, nx - 1)  # streamed from real columns only (no periodic seam)
+    rows = np.arange(0, nr - 1)  # streamed from real rows or the axis mirror (no wall)
+    X, R = np.meshgrid(cols.astype(float), I.radii(nr)[rows], indexing="xy")
+    V = P.polyvander2d(X.ravel(), R.ravel(), [2, 2])
+    coef = []
+    for c in range(4):
+        vals = mom[c][np.ix_(rows, cols)].ravel()
+        cf, *_ = np.linalg.lstsq(V, vals, rcond=None)
+        assert np.abs(V @ cf - vals).max() < 1e-14  # the streamed moments are that polynomial
+        coef.append(cf.reshape(3, 3))
+    checked = 0
+    for j in range(0, nr - 2):
+        r = I.radii(nr)[j]
+        for i in range(2, nx - 2):
+            d = [P.polyval2d(i, r, P.polyder(coef[1], axis=1)),
+                 P.polyval2d(i, r, P.polyder(coef[2], axis=1)),
+                 P.polyval2d(i, r, P.polyder(coef[2], axis=0)),
+                 P.polyval2d(i, r, P.polyder(coef[3], axis=1))]
+            fo, go, _ = orc.collide_node(fs[:, j, i], gs[:, j, i], r, np.array(d), nu, alpha, Cs, 0.3, True)
+            np.testing.assert_allclose(f1[:, j, i], fo, rtol=0, atol=1e-14)
+            np.testing.assert_allclose(g1[:, j, i], go, rtol=0, atol=1e-14)
+            checked += 1
+    assert checked == (nr - 2) * (nx - 4)
+
+
 # ---- boundary rules on tiny lattices ----------------------------------------
 
 def _tiny(orc, nx=3, nr=3, **kw):
@@ -300,6 +374,32 @@ def test_inlet_ghost_is_equilibrium(orc):
     # diagonal from row 1 into row 2 at the inlet uses row 1's profile
     rho_b = f[:, 1, 0].sum()
     assert fs[5, 2, 0] == pytest.approx(orc.feq(rho_b, u_in[1], 0.0)[5], abs=1e-16)
+
+
+def test_inlet_noise_enters_flowing_rows_only(orc):
+    """The inlet perturbation xi_{j,t} of the pull at step t is added on rows whose profile flows.
+
+    Rows with zero inlet velocity (the coflow-free part of a nozzle) get no
+    noise; the pull of step t uses the generator's value at counter (t, j).
+    """
+    nx, nr, seed, amp = 3, 3, 77, 1e-3
+    cfg = I.LatticeConfig(nx=nx, nr=nr, bc_in="inlet", bc_out="outflow", bc_top="wall",
+                          noise_amp=amp, seed=seed)
+    o = orc.Oracle(cfg)
+    u_in = np.array([0.05, 0.0, 0.02])
+    T_in = np.array([3.0, 2.0, 1.0])
+    o.set_inlet(u_in, T_in)
+    rng = np.random.default_rng(12)
+    f = 0.05 + 0.1 * rng.random((9, nr, nx))
+    g = 0.2 + 0.1 * rng.random((4, nr, nx))
+    for t in (9, 10):
+        o.set_state(f, g, t)
+        fs, gs = o.streamed()
+        for j in range(nr):
+            u = u_in[j] + (orc.inlet_noise(seed, t, j, amp) if u_in[j] != 0.0 else 0.0)
+            assert fs[1, j, 0] == pytest.approx(orc.feq(f[:, j, 0].sum(), u, 0.0)[1], abs=1e-16)
+            assert gs[0, j, 0] == pytest.approx(orc.geq(T_in[j], u, 0.0)[0], abs=1e-16)
+        assert abs(fs[1, 0, 0] - orc.feq(f[:, 0, 0].sum(), u_in[0], 0.0)[1]) > 1e-6  # the noise is there
 
 
 def test_outflow_holds_reference_density(orc):
