@@ -133,10 +133,9 @@ class ClockSampler:
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1002_3028_gb300 import replicas
+
+    return replicas.world()
 
 
 def cpu_baseline(ws, budget_s: float, label: str):
@@ -216,16 +215,12 @@ def run_reference(args):
 def run_gpu(args):
     import torch
 
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
+    from paper_1002_3028_gb300 import autotune, lbm, replicas
 
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ws, rank, local = dist_env()
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
-
-    from paper_1002_3028_gb300 import autotune, lbm
+    replicas.init("nccl", device)  # replicas only: no collective on the data path
 
     works = workloads_by_name(args.workload)
     label = workload_label(args.workload, works)
@@ -248,8 +243,7 @@ def run_gpu(args):
         target.set_launch(max(args.band, 0), args.warps)
 
     def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
+        replicas.barrier()
         torch.cuda.synchronize(device)
 
     # warm-up, then the device-timed region: K steps bracketed by events on the launching stream
@@ -263,12 +257,8 @@ def run_gpu(args):
         ev1.record(stream)
         ev1.synchronize()
     barrier()
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        t = torch.tensor([ms], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    mlups = nodes * args.steps * ws / (ms * 1e-3) / 1e6
+    ms, units = replicas.combine(ev0.elapsed_time(ev1), nodes * args.steps, device)
+    mlups = units / (ms * 1e-3) / 1e6
     per_launch_s = ms * 1e-3 / args.steps
     bpl = POPS * 2 * BYTES_PER_VALUE[args.storage]
     achieved = bpl * nodes / per_launch_s / 1e9
@@ -305,18 +295,15 @@ def run_gpu(args):
     e1.record(stream)
     e1.synchronize()
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms, e2e_units = replicas.combine(e0.elapsed_time(e1), nodes * args.steps, device)
     h2d = sum((fh.numel() + gh.numel()) * 8 for fh, gh in host_states)
     d2h = sum(oh.numel() * 4 for _, oh in outs)
-    e2e = {"value": nodes * args.steps * ws / (e2e_ms * 1e-3) / 1e6, "unit": "MLUPS",
+    e2e = {"value": e2e_units / (e2e_ms * 1e-3) / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
            "note": "initial states uploaded, K steps, fields downloaded; copies amortised over K"}
 
     if rank != 0:
+        replicas.finish()
         return 0
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
@@ -345,8 +332,7 @@ def run_gpu(args):
         "device_flags": flags,
     }
     print(json.dumps(line), flush=True)
-    if ws > 1:
-        torch.distributed.destroy_process_group()
+    replicas.finish()
     return 0
 
 

@@ -227,6 +227,29 @@ LBM_API int lbm_set_state(lbm_lattice *h, const double *dev_f, const double *dev
                   lbm_stream stream);
 
 /*
+ * Checkpoint and resume, bit for bit.  The paper has no counterpart (its
+ * runs are single uninterrupted integrations of Eq. 1); a checkpoint is the
+ * stored state exactly as the step kernel keeps it, so a resumed lattice
+ * continues exactly as an uninterrupted one would.
+ *
+ * lbm_checkpoint_bytes: size of a checkpoint, 13 * nr * nx values of the
+ *   storage type (8, 4 or 2 bytes).
+ * lbm_save: copy the stored populations, as deviations from rest
+ *   (f_k - w_k rho0 and g_k - T0 / 4, in the storage type), into dev_out,
+ *   caller device memory of lbm_checkpoint_bytes bytes, layout
+ *   [q][j][i] with q = f0..f8, g0..g3.  The step counter is read with
+ *   lbm_get_step.  Asynchronous on the stream.
+ * lbm_restore: the reverse, into a lattice with the same description
+ *   (size and storage), and set its step counter to step (>= 0); the
+ *   boundary ghosts are recomputed.  The next lbm_diagnostics residual has
+ *   no previous state.  Returns LBM_ERR_INVALID_ARG for a NULL buffer or a
+ *   negative step.
+ */
+LBM_API int lbm_checkpoint_bytes(const lbm_lattice *h, size_t *bytes);
+LBM_API int lbm_save(lbm_lattice *h, void *dev_out, lbm_stream stream);
+LBM_API int lbm_restore(lbm_lattice *h, const void *dev_in, int64_t step, lbm_stream stream);
+
+/*
  * Launch shape of the step kernel: CTAs of warps_per_cta warps (1..8), one
  * warp per tile of 64 columns (32 for LBM_F64) x band_rows rows.
  * band_rows >= 1 fixes the band height; 0 lets the library choose it from

@@ -103,6 +103,9 @@ def lib(build: bool = True):
             L.lbm_get_fields.argtypes = [vp, vp, i32, vp]
             L.lbm_get_state.argtypes = [vp, vp, vp, vp]
             L.lbm_set_state.argtypes = [vp, vp, vp, i64, vp]
+            L.lbm_checkpoint_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+            L.lbm_save.argtypes = [vp, vp, vp]
+            L.lbm_restore.argtypes = [vp, vp, i64, vp]
             L.lbm_set_launch.argtypes = [vp, i32, i32]
             L.lbm_get_launch.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
             L.lbm_check.argtypes = [vp, C.POINTER(i32)]
@@ -281,6 +284,32 @@ class Lattice:
         _check(self._L.lbm_set_state(self._h, C.c_void_p(f.data_ptr()), C.c_void_p(g.data_ptr()),
                                      int(step), _stream_ptr(stream)), "lbm_set_state")
         # keep the inputs alive until the conversion kernel has run
+        torch.cuda.current_stream(self.device).synchronize() if stream is None else stream.synchronize()
+
+    def save(self, stream=None):
+        """Checkpoint: (stored deviations (13, nr, nx) in the storage type, step count); exact."""
+        import torch
+
+        n = C.c_size_t()
+        _check(self._L.lbm_checkpoint_bytes(self._h, C.byref(n)), "lbm_checkpoint_bytes")
+        dt = {"f64": torch.float64, "f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[self.storage]
+        out = torch.empty((13, self.nr, self.nx), dtype=dt, device=self.device)
+        assert out.numel() * out.element_size() == n.value
+        _check(self._L.lbm_save(self._h, C.c_void_p(out.data_ptr()), _stream_ptr(stream)), "lbm_save")
+        return out, self.step_count
+
+    def restore(self, planes, step: int, stream=None):
+        """Resume from a checkpoint taken by ``save`` on a lattice of the same size and storage."""
+        import torch
+
+        n = C.c_size_t()
+        _check(self._L.lbm_checkpoint_bytes(self._h, C.byref(n)), "lbm_checkpoint_bytes")
+        if tuple(planes.shape) != (13, self.nr, self.nx) or planes.numel() * planes.element_size() != n.value:
+            raise ValueError("checkpoint does not match this lattice")
+        planes = planes.to(self.device).contiguous()
+        _check(self._L.lbm_restore(self._h, C.c_void_p(planes.data_ptr()), int(step), _stream_ptr(stream)),
+               "lbm_restore")
+        # keep the input alive until the copies have run
         torch.cuda.current_stream(self.device).synchronize() if stream is None else stream.synchronize()
 
 

@@ -255,3 +255,39 @@ def test_fields_float32_output(lbm, orc):
     Fo = o.fields()
     F32 = g.fields(dtype=torch.float32)
     assert max(fields_rel(F32.double(), Fo)) < 1e-6
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+def test_checkpoint_resume_is_exact(lbm, storage):
+    """Save mid-run, restore into a fresh lattice, continue: bit for bit the uninterrupted run."""
+    w = workload(90, 33)
+    a = lbm.Lattice.from_workload(w, storage)
+    a.step(40)
+    planes, step = a.save()
+    assert step == 40
+    b = lbm.Lattice.from_workload(w, storage)
+    b.restore(planes.clone(), step)
+    assert b.step_count == 40
+    a.step(25)
+    b.step(25)
+    pa, _ = a.save()
+    pb, _ = b.save()
+    assert torch.equal(pa, pb)
+    assert torch.equal(a.fields(), b.fields())
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+def test_state_roundtrip_through_fp64_resumes_closely(lbm, storage):
+    """get_state / set_state round trips through absolute FP64 values: within a rounding of the storage."""
+    w = workload(90, 33)
+    a = lbm.Lattice.from_workload(w, storage)
+    a.step(40)
+    f, g = a.get_state()
+    b = lbm.Lattice.from_workload(w, storage)
+    b.set_state(f, g, a.step_count)
+    a.step(25)
+    b.step(25)
+    tol = {"f64": 1e-15, "f32": 1e-6, "f16": 1e-3}[storage]
+    fa, ga = a.get_state()
+    fb, gb = b.get_state()
+    assert (fa - fb).abs().max().item() < tol and (ga - gb).abs().max().item() < tol
