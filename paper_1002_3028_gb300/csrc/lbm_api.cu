@@ -66,6 +66,7 @@ struct Layout {
     size_t off_uin_d, off_tin_d, off_uin_f, off_tin_f;
     size_t off_nu_d, off_al_d, off_nu_f, off_al_f;
     size_t off_status;
+    size_t off_sync;  // multi-step launch: work counter, then one counter per warp tile
     size_t off_diag;  // diagnostics scratch: block partials, then the folded result
     size_t total;
 };
@@ -121,6 +122,8 @@ Layout make_layout(const lbm_desc *d)
     L.off_nu_f = o; o += tf;
     L.off_al_f = o; o += tf;
     L.off_status = o; o += kAlign;
+    // warp tiles are at least 32 columns by one row
+    L.off_sync = o; o += align_up((size_t)4 * (1 + (size_t)((d->nx + 31) / 32) * (size_t)d->nr));
     L.off_diag = o; o += align_up((size_t)(lbm::DIAG_MAX_BLOCKS + 1) * lbm::DIAG_SLOTS * sizeof(double));
     L.total = o;
     return L;
@@ -142,7 +145,8 @@ struct lbm_lattice {
     double T_lo, T_hi;
     bool prev_valid;       // the other buffer holds the state one step earlier
     int band, warps;       // launch shape; band 0 = chosen from the occupancy
-    int band_eff, ctas;    // band and CTA count used by lbm_step
+    int band_eff, ctas;    // band and CTA count of a one-step lbm_step launch
+    int ctas_max;          // CTAs resident on the device at once (persistent grid)
     int device, sms;
 
     void *buf(int b) const { return mem + L.off_buf[b]; }
@@ -234,10 +238,10 @@ int plan_launch(lbm_lattice *h)
     int per_sm = 0;
     cudaError_t e;
     switch (h->d.storage) {
-    case LBM_F64: e = lbm::occupancy_step_f64(h->warps, &per_sm); break;
-    case LBM_F32: e = lbm::occupancy_step_f32(h->warps, &per_sm); break;
-    case LBM_F16: e = lbm::occupancy_step_f16(h->warps, &per_sm); break;
-    default: e = lbm::occupancy_step_bf16(h->warps, &per_sm); break;
+    case LBM_F64: e = lbm::occupancy_run_f64(h->warps, &per_sm); break;
+    case LBM_F32: e = lbm::occupancy_run_f32(h->warps, &per_sm); break;
+    case LBM_F16: e = lbm::occupancy_run_f16(h->warps, &per_sm); break;
+    default: e = lbm::occupancy_run_bf16(h->warps, &per_sm); break;
     }
     if (e != cudaSuccess)
         return cuda_fail(e, "occupancy query");
@@ -253,10 +257,8 @@ int plan_launch(lbm_lattice *h)
         h->band_eff = (int)std::min<int64_t>(16, std::max<int64_t>(4, band));
     }
     const int64_t ntiles = (int64_t)nstrips * ((h->d.nr + h->band_eff - 1) / h->band_eff);
-    const int64_t ctas = (ntiles + h->warps - 1) / h->warps;
-    if (ctas > INT32_MAX)
-        return fail(LBM_ERR_INVALID_ARG, "too many tiles");
-    h->ctas = (int)ctas;
+    h->ctas_max = per_sm * std::max(1, h->sms);
+    h->ctas = (int)std::min<int64_t>(h->ctas_max, (ntiles + h->warps - 1) / h->warps);
     return LBM_OK;
 }
 
@@ -683,19 +685,36 @@ int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
     if (h->batch)
         return fail(LBM_ERR_INVALID_ARG, "the lattice belongs to a batch: step the batch");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    for (int n = 0; n < nsteps; ++n) {
-        cudaError_t e;
-        switch (h->d.storage) {
-        case LBM_F64: e = lbm::launch_step_f64(params_d(h), h->warps, h->ctas, s); break;
-        case LBM_F32: e = lbm::launch_step_f32(params_f(h), h->warps, h->ctas, s); break;
-        case LBM_F16: e = lbm::launch_step_f16(params_f(h), h->warps, h->ctas, s); break;
-        default: e = lbm::launch_step_bf16(params_f(h), h->warps, h->ctas, s); break;
+    const lbm_desc &d = h->d;
+    const int nstrips = (d.nx + strip_cols(d.storage) - 1) / strip_cols(d.storage);
+    const int64_t ntiles = (int64_t)nstrips * ((d.nr + h->band_eff - 1) / h->band_eff);
+    // steps per launch: the work counter stays below 2^31
+    const int64_t per_launch = std::max<int64_t>(1, ((int64_t)1 << 31) / std::max<int64_t>(1, 2 * ntiles));
+    unsigned *sync = h->at<unsigned>(h->L.off_sync);
+    lbm::RunCtl ctl;
+    ctl.counter = sync;
+    ctl.flags = sync + 1;
+    ctl.radius = h->band_eff >= 2 ? 1 : 2;
+    ctl.wrap = d.bc_in == LBM_IN_PERIODIC ? 1 : 0;
+    for (int64_t done = 0; done < nsteps;) {
+        const int m = (int)std::min<int64_t>(per_launch, nsteps - done);
+        cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)4 * (size_t)(1 + ntiles), s);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "work counter reset");
+        ctl.nsteps = m;
+        const int ctas = (int)std::min<int64_t>(h->ctas_max, (m * ntiles + h->warps - 1) / h->warps);
+        switch (d.storage) {
+        case LBM_F64: e = lbm::launch_run_f64(params_d(h), ctl, h->warps, ctas, s); break;
+        case LBM_F32: e = lbm::launch_run_f32(params_f(h), ctl, h->warps, ctas, s); break;
+        case LBM_F16: e = lbm::launch_run_f16(params_f(h), ctl, h->warps, ctas, s); break;
+        default: e = lbm::launch_run_bf16(params_f(h), ctl, h->warps, ctas, s); break;
         }
         if (e != cudaSuccess)
             return cuda_fail(e, "step kernel launch");
-        h->cur = 1 - h->cur;
-        h->step += 1;
+        h->cur ^= (m & 1);
+        h->step += m;
         h->prev_valid = true;
+        done += m;
     }
     return LBM_OK;
 }

@@ -13,8 +13,9 @@ namespace lbm {
 // Launchers, one set per storage type (defined in lbm_step_<type>.cu).
 // Each returns the cudaError_t of the launch.
 #define LBM_DECLARE_LAUNCHERS(TAG, C)                                                                  \
-    cudaError_t launch_step_##TAG(const StepParams<C> &p, int warps_per_cta, int ctas, cudaStream_t s); \
-    cudaError_t occupancy_step_##TAG(int warps_per_cta, int *ctas_per_sm);                             \
+    cudaError_t launch_run_##TAG(const StepParams<C> &p, const RunCtl &ctl, int warps_per_cta, int ctas,  \
+                                 cudaStream_t s);                                                      \
+    cudaError_t occupancy_run_##TAG(int warps_per_cta, int *ctas_per_sm);                              \
     cudaError_t launch_batch_##TAG(const TileRef *tiles, int ntiles, StepParams<C> *lattices, int nlat,     \
                                    int warps_per_cta, cudaStream_t s);                                 \
     cudaError_t occupancy_batch_##TAG(int warps_per_cta, int *ctas_per_sm);                            \

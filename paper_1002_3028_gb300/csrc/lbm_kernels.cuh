@@ -87,11 +87,14 @@ struct alignas(16) StepParams {
 };
 
 // ---- storage conversions -----------------------------------------------------
+// Population loads go through L2 (ld.global.cg): a multi-step launch reads
+// buffers that other warps of the same launch wrote, which the read-only
+// and L1 paths may not see.
 template <class S, class C> __device__ __forceinline__ C load_as(const S *p);
-template <> __device__ __forceinline__ double load_as<double, double>(const double *p) { return __ldg(p); }
-template <> __device__ __forceinline__ float load_as<float, float>(const float *p) { return __ldg(p); }
-template <> __device__ __forceinline__ float load_as<__half, float>(const __half *p) { return __half2float(__ldg(p)); }
-template <> __device__ __forceinline__ float load_as<__nv_bfloat16, float>(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+template <> __device__ __forceinline__ double load_as<double, double>(const double *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ float load_as<float, float>(const float *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ float load_as<__half, float>(const __half *p) { return __half2float(__ldcg(p)); }
+template <> __device__ __forceinline__ float load_as<__nv_bfloat16, float>(const __nv_bfloat16 *p) { return __bfloat162float(__ldcg(p)); }
 
 template <class S, class C> __device__ __forceinline__ C load_as_shared(const S *p);
 template <> __device__ __forceinline__ double load_as_shared<double, double>(const double *p) { return *p; }
@@ -593,29 +596,70 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// The chunks one lane copies for every row of a tile: their element offsets
-// within a row's pull (plane, source-row shift and column); chunk
-// t = lane + 32 m lands at stage element t * E.  Offsets are 32-bit (the
-// library caps the lattice so that 13 planes stay below 2^31 elements).
+// The chunks one lane copies for every row of a tile.  Every plane copies
+// its 32 NV own columns (OPP chunks); the 16-byte halo chunk on the left is
+// copied only for the six planes that read it (f1, f5, f8, g0 pull from
+// x - 1; f2, f4, f5, f8 enter rho u_r at column -1), the one on the right
+// only for f3, f6, f7, g2 and f2, f4, f6, f7 likewise: 13 OPP + 12 chunks a
+// row instead of 13 (OPP + 2).  Chunk t = lane + 32 m is an own chunk for
+// t < 13 OPP (plane t / OPP, window chunk 1 + t % OPP), else halo chunk
+// t - 13 OPP of the table below.  It lands at window element
+// plane * W + chunk * E of the stage; unused halo slots are never read.
+// Global offsets are 32-bit (the library caps the lattice so that 13 planes
+// stay below 2^31 elements).
 template <class S, int NV>
 struct CopyPlan {
-    static constexpr int TOTAL = 13 * Win<S, NV>::CH;
+    using Wn = Win<S, NV>;
+    static constexpr int OPP = 32 * NV / Wn::E;  // own chunks per plane
+    static constexpr int OWN = 13 * OPP;
+    static constexpr int TOTAL = OWN + 12;
     static constexpr int PER_LANE = (TOTAL + 31) / 32;
-    int goff[PER_LANE];
+    static_assert(32 % OPP == 0, "own chunks of a plane must tile a warp's lanes");
+    static_assert(32 * (PER_LANE - 1) <= OWN, "only the last copy of a lane may be a halo chunk");
+    int goff[PER_LANE];  // element offset in the source buffer (row 0)
+    int sbase;           // stage element of this lane's own chunk in copy 0
+    int slast;           // stage element of this lane's chunk in copy PER_LANE - 1
 };
+
+// plane of halo chunk h: left halos (window chunk 0) for h < 6, right halos
+// (last window chunk) for h >= 6
+__device__ __forceinline__ int halo_plane(int h)
+{
+    constexpr unsigned long long packed = 1ull | (2ull << 4) | (4ull << 8) | (5ull << 12) | (8ull << 16) |
+                                          (9ull << 20) | (2ull << 24) | (3ull << 28) | (4ull << 32) |
+                                          (6ull << 36) | (7ull << 40) | (11ull << 44);
+    return (int)((packed >> (4 * h)) & 15ull);
+}
+
+template <class S, int NV>
+__device__ __forceinline__ void chunk_of(int t, int &q, int &c)
+{
+    using CP = CopyPlan<S, NV>;
+    if (t < CP::OWN) {
+        q = t / CP::OPP;
+        c = 1 + t % CP::OPP;
+    } else {
+        const int h = t - CP::OWN;
+        q = halo_plane(h);
+        c = h < 6 ? 0 : Win<S, NV>::CH - 1;
+    }
+}
 
 template <class S, int NV, class C>
 __device__ __forceinline__ CopyPlan<S, NV> make_copy_plan(const StepParams<C> &p, int x0, int lane)
 {
     using Wn = Win<S, NV>;
-    CopyPlan<S, NV> cp;
+    using CP = CopyPlan<S, NV>;
+    CP cp;
 #pragma unroll
-    for (int m = 0; m < CopyPlan<S, NV>::PER_LANE; ++m) {
-        const int t = min(lane + 32 * m, CopyPlan<S, NV>::TOTAL - 1);
-        const int q = t / Wn::CH;
-        const int c = t - q * Wn::CH;
+    for (int m = 0; m < CP::PER_LANE; ++m) {
+        int q, c;
+        chunk_of<S, NV>(min(lane + 32 * m, CP::TOTAL - 1), q, c);
         cp.goff[m] = q * (int)p.plane - plane_ey(q) * p.pitch + (x0 - Wn::H + c * Wn::E + PAD_COLS);
+        if (m == CP::PER_LANE - 1)
+            cp.slast = q * Wn::W + c * Wn::E;
     }
+    cp.sbase = (lane / CP::OPP) * Wn::W + (1 + lane % CP::OPP) * Wn::E;
     return cp;
 }
 
@@ -624,11 +668,15 @@ template <class S, int NV, class C>
 __device__ __forceinline__ void issue_row(const StepParams<C> &p, const S *src, S *stage, const CopyPlan<S, NV> &cp,
                                           int r, int lane)
 {
+    using CP = CopyPlan<S, NV>;
     const int row = (r + 1) * p.pitch;
 #pragma unroll
-    for (int m = 0; m < CopyPlan<S, NV>::PER_LANE; ++m)
-        if (lane + 32 * m < CopyPlan<S, NV>::TOTAL)
-            cp_async16(stage + (lane + 32 * m) * Win<S, NV>::E, src + (unsigned)(row + cp.goff[m]));
+    for (int m = 0; m < CP::PER_LANE; ++m) {
+        // copies before the last hold own chunks only: 32 m / OPP whole planes further on
+        const int so = (m < CP::PER_LANE - 1) ? cp.sbase + (32 * m / CP::OPP) * Win<S, NV>::W : cp.slast;
+        if (m < CP::PER_LANE - 1 || lane + 32 * m < CP::TOTAL)
+            cp_async16(stage + so, src + (unsigned)(row + cp.goff[m]));
+    }
 }
 
 // population q of strip column col (-1 and 32 NV are the columns beside the strip)
@@ -666,7 +714,7 @@ __device__ __forceinline__ C stage_jr(const S *stage, int col)
 // collide row j of the tile from its stage and write it (and its ghosts)
 template <class S, int NV, class C>
 __device__ __forceinline__ void collide_row(const StepParams<C> &p, const S *src, S *__restrict__ dst, const S *st,
-                                            int x0, int lane, int j, const Mom<Vec<C, NV>> &mp,
+                                            int x0, int lane, int j, int64_t t, const Mom<Vec<C, NV>> &mp,
                                             const Mom<Vec<C, NV>> &mc, const Mom<Vec<C, NV>> &mn)
 {
     using V = Vec<C, NV>;
@@ -713,7 +761,7 @@ __device__ __forceinline__ void collide_row(const StepParams<C> &p, const S *src
             for (int k = 0; k < 4; ++k)
                 dst[o + (9 + k) * pl] = store_as<S, C>(go[k][c]);
             if (i == 0 || i == p.nx - 1 || j == 0 || j == p.nr - 1)
-                write_ghosts<S, C>(p, dst, i, j, p.step + 1);
+                write_ghosts<S, C>(p, dst, i, j, t + 1);
         }
     }
 }
@@ -725,7 +773,7 @@ __device__ __forceinline__ void collide_row(const StepParams<C> &p, const S *src
 // the two being read: it held row idx - 2.)
 template <class S, int NV, class C>
 __device__ __forceinline__ void step_tile(const StepParams<C> &p, const S *__restrict__ src, S *__restrict__ dst,
-                                          S *wsm, int tile, int lane)
+                                          S *wsm, int tile, int lane, int64_t t)
 {
     using Wn = Win<S, NV>;
     using V = Vec<C, NV>;
@@ -767,13 +815,13 @@ __device__ __forceinline__ void step_tile(const StepParams<C> &p, const S *__res
                 mp = ghost_bottom<C, V>(p, mr);
             mc = mr;
         } else {
-            collide_row<S, NV, C>(p, src, dst, wsm + ((idx - 1) % NSTAGE) * Wn::STAGE, x0, lane, r - 1, mp, mc, mr);
+            collide_row<S, NV, C>(p, src, dst, wsm + ((idx - 1) % NSTAGE) * Wn::STAGE, x0, lane, r - 1, t, mp, mc, mr);
             mp = mc;
             mc = mr;
         }
     }
     if (j1 == p.nr)
-        collide_row<S, NV, C>(p, src, dst, wsm + ((nrows - 1) % NSTAGE) * Wn::STAGE, x0, lane, p.nr - 1, mp, mc,
+        collide_row<S, NV, C>(p, src, dst, wsm + ((nrows - 1) % NSTAGE) * Wn::STAGE, x0, lane, p.nr - 1, t, mp, mc,
                               ghost_top<C, V>(p, mc));
     cp_async_wait<0>();
     __syncwarp();
@@ -786,19 +834,115 @@ constexpr int step_smem_per_warp()
     return Stages<NV>::value * Win<S, NV>::STAGE * (int)sizeof(S);
 }
 
+// ---- many steps of one lattice in one launch ----------------------------------------
+// lbm_step runs all its steps in one persistent launch.  Warps take warp
+// tiles from a counter in step-major order (work item n = k * ntiles + tile
+// for sub-step k).  A tile of sub-step k > 0 reads what the tiles around it
+// wrote in sub-step k - 1 and overwrites what they read there: rows within
+// one band (two bands for one-row bands) and columns within one strip
+// (wrapping around for periodic ends).  So before starting it waits until
+// those neighbour tiles count sub-step k - 1 as done.  Each lane adds one
+// to its tile's counter with release semantics after its last store, so a
+// tile is done with sub-step k - 1 once its counter reaches 32 k; the
+// waiting lanes each read every neighbour counter, then fence (acquire).
+// Every neighbour's work item precedes the waiting one in the counter
+// order, so it was taken by a warp that is already running; a warp works on
+// its items in counter order, and the lowest unfinished item never waits on
+// a later one, so the waits end.  Each wait is bounded all the
+// same; a wait that runs out raises LBM_STATUS_TIMEOUT in the lattice's
+// status word and every warp stops taking work.
+constexpr int STATUS_TIMEOUT = 1;
+constexpr int RUN_SPIN_LIMIT = 1 << 22;  // polls of at most ~1 us: a few seconds
+
+struct RunCtl {
+    unsigned *counter;  // work items taken (zeroed before the launch)
+    unsigned *flags;    // per warp tile: 32 x sub-steps done (zeroed before the launch)
+    int nsteps;         // sub-steps of this launch
+    int radius;         // neighbour bands a tile depends on
+    int wrap;           // strips wrap around (periodic axial ends)
+};
+
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned *a)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add(unsigned *a, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;\n" ::"l"(a), "r"(v) : "memory");
+}
+
+// Every lane waits until the tiles around `tile` have finished sub-step
+// k - 1: the counters are polled with relaxed loads (all in flight at once)
+// and, once every one is high enough, a fence gives the polls acquire
+// semantics.  Returns false if the wait runs out or another warp's wait ran
+// out (the status word is read only while waiting).
+template <class C>
+__device__ bool wait_neighbours(const StepParams<C> &p, const RunCtl &ctl, int tile, int k)
+{
+    const int s = tile % p.nstrips, b = tile / p.nstrips;
+    const int nbands = (p.nr + p.band - 1) / p.band;
+    const unsigned want = 32u * (unsigned)k;
+    for (int it = 0;; ++it) {
+        bool ok = true;
+        for (int db = -ctl.radius; db <= ctl.radius; ++db) {
+            const int bb = b + db;
+            if (bb < 0 || bb >= nbands)
+                continue;
+#pragma unroll
+            for (int ds = -1; ds <= 1; ++ds) {
+                int ss = s + ds;
+                if (ctl.wrap)
+                    ss = ss < 0 ? ss + p.nstrips : (ss >= p.nstrips ? ss - p.nstrips : ss);
+                if (ss < 0 || ss >= p.nstrips)
+                    continue;
+                ok &= (int)(ld_relaxed(ctl.flags + bb * p.nstrips + ss) - want) >= 0;
+            }
+        }
+        if (__all_sync(0xffffffffu, ok)) {
+            __threadfence();
+            return true;
+        }
+        if (it >= RUN_SPIN_LIMIT || (*static_cast<volatile int *>(p.status) & STATUS_TIMEOUT))
+            return false;
+        __nanosleep(it < 8 ? 64 : 512);
+    }
+}
+
 template <class S, class C>
-__global__ void __launch_bounds__(256) step_kernel(const __grid_constant__ StepParams<C> p)
+__global__ void __launch_bounds__(256) step_run_kernel(const __grid_constant__ StepParams<C> p, const RunCtl ctl)
 {
     constexpr int NV = NodesPerLane<C>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int wpc = blockDim.x >> 5;
-    const int tile = blockIdx.x * wpc + warp;
-    if (tile >= p.ntiles)
-        return;  // whole warp
     S *wsm = reinterpret_cast<S *>(smem_raw) + (size_t)warp * Stages<NV>::value * Win<S, NV>::STAGE;
-    step_tile<S, NV, C>(p, static_cast<const S *>(p.src), static_cast<S *>(p.dst), wsm, tile, lane);
+    const unsigned total = (unsigned)ctl.nsteps * (unsigned)p.ntiles;
+    unsigned n = 0;
+    if (lane == 0)
+        n = atomicAdd(ctl.counter, 1u);
+    n = __shfl_sync(0xffffffffu, n, 0);
+    while (n < total) {
+        // take the next work item now: its latency hides behind this tile
+        // (items are still started in counter order by each warp)
+        unsigned next = 0;
+        if (lane == 0)
+            next = atomicAdd(ctl.counter, 1u);
+        const int k = (int)(n / (unsigned)p.ntiles);
+        const int tile = (int)(n - (unsigned)k * (unsigned)p.ntiles);
+        if (k > 0 && !wait_neighbours<C>(p, ctl, tile, k)) {
+            if (lane == 0)
+                atomicOr(p.status, STATUS_TIMEOUT);
+            break;  // whole warp
+        }
+        const S *src = static_cast<const S *>((k & 1) ? p.dst : p.src);
+        S *dst = static_cast<S *>((k & 1) ? const_cast<void *>(p.src) : p.dst);
+        step_tile<S, NV, C>(p, src, dst, wsm, tile, lane, p.step + k);
+        red_release_add(ctl.flags + tile, 1u);
+        n = __shfl_sync(0xffffffffu, next, 0);
+    }
 }
 
 // ---- many lattices in one launch --------------------------------------------------------
@@ -835,7 +979,7 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const TileRef *__restri
     __syncwarp();
     const StepParams<C> &p = *pw;
     S *wsm = reinterpret_cast<S *>(smem_raw + wpc * sizeof(StepParams<C>)) + (size_t)warp * Stages<NV>::value * Win<S, NV>::STAGE;
-    step_tile<S, NV, C>(p, static_cast<const S *>(p.src), static_cast<S *>(p.dst), wsm, t.tile, lane);
+    step_tile<S, NV, C>(p, static_cast<const S *>(p.src), static_cast<S *>(p.dst), wsm, t.tile, lane, p.step);
 }
 
 template <class S, class C>

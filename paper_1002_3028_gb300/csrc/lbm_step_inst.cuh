@@ -7,24 +7,26 @@
 
 namespace lbm {
 
-cudaError_t LBM_CAT(launch_step_, LBM_TAG)(const StepParams<LBM_C> &p, int warps_per_cta, int ctas, cudaStream_t s)
+cudaError_t LBM_CAT(launch_run_, LBM_TAG)(const StepParams<LBM_C> &p, const RunCtl &ctl, int warps_per_cta, int ctas,
+                                          cudaStream_t s)
 {
-    if (p.ntiles <= 0)
+    if (p.ntiles <= 0 || ctl.nsteps <= 0)
         return cudaSuccess;
     const int smem = warps_per_cta * step_smem_per_warp<LBM_S, LBM_C>();
-    step_kernel<LBM_S, LBM_C><<<ctas, 32 * warps_per_cta, smem, s>>>(p);
+    step_run_kernel<LBM_S, LBM_C><<<ctas, 32 * warps_per_cta, smem, s>>>(p, ctl);
     return cudaGetLastError();
 }
 
 // allows the dynamic shared memory of the widest CTA and reports how many
 // CTAs of the given width fit on one SM
-cudaError_t LBM_CAT(occupancy_step_, LBM_TAG)(int warps_per_cta, int *ctas_per_sm)
+cudaError_t LBM_CAT(occupancy_run_, LBM_TAG)(int warps_per_cta, int *ctas_per_sm)
 {
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<LBM_S, LBM_C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(step_run_kernel<LBM_S, LBM_C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          8 * step_smem_per_warp<LBM_S, LBM_C>());
     if (e != cudaSuccess)
         return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, step_kernel<LBM_S, LBM_C>, 32 * warps_per_cta,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, step_run_kernel<LBM_S, LBM_C>,
+                                                         32 * warps_per_cta,
                                                          warps_per_cta * step_smem_per_warp<LBM_S, LBM_C>());
 }
 
