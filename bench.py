@@ -8,7 +8,7 @@ kernel (tiles of step t + 1 start as soon as their neighbours finished
 step t).  The two population buffers
 (436 MB in FP32) are larger than the 129 MB L2, so no flush is needed
 between steps.  ``--workload ensemble`` steps 256 ragged jets as one batch
-(one launch per step, CUDA-graph replay); ``--workload jetNXxNR`` any size.
+(persistent multi-step launches, CUDA-graph replay); ``--workload jetNXxNR`` any size.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on the host cores on the same workload instead.
@@ -215,16 +215,17 @@ def run_reference(args):
 
 
 def step_launches(lats, storage: str, launch, steps: int) -> int:
-    """Kernels launched by `steps` steps: one lattice runs its steps in persistent launches
-    of up to 2^31 / (2 x warp tiles) steps each; a batch launches its step kernel and the
-    parameter advance once per step."""
-    if len(lats) > 1:
-        return 2 * steps
-    lat, band = lats[0], launch[0]
+    """Kernels launched by `steps` steps.  One lattice runs its steps in persistent launches
+    of up to 2^31 / (2 x warp tiles) steps each.  A batch replays a captured launch of 64
+    steps and runs the rest in one launch; each launch is followed by the parameter advance."""
     strip = 32 if storage == "f64" else 64
-    ntiles = -(-lat.nx // strip) * -(-lat.nr // band)
+    band = launch[0]
+    ntiles = sum(-(-lat.nx // strip) * -(-lat.nr // band) for lat in lats)
     per_launch = max(1, (1 << 31) // (2 * ntiles))
-    return -(-steps // per_launch)
+    if len(lats) == 1:
+        return -(-steps // per_launch)
+    graph = min(64, per_launch)
+    return 2 * (steps // graph + (1 if steps % graph else 0))
 
 
 def run_gpu(args):
@@ -245,7 +246,7 @@ def run_gpu(args):
     if len(lats) == 1:
         target = lats[0]
         step = target.step
-    else:  # an ensemble: one batch, one launch per step, graph replay
+    else:  # an ensemble: one batch, persistent multi-step launches, graph replay
         target = lbm.Batch(args.storage)
         for lat in lats:
             target.add(lat)

@@ -151,8 +151,13 @@ LBM_API int lbm_set_properties(lbm_lattice *h, const double *nu, const double *a
                        double T_lo, double T_hi, lbm_stream stream);
 
 /*
- * Advance nsteps >= 0 time steps (Eq. 1), one fused kernel launch per step.
- * Asynchronous; returns LBM_ERR_CUDA if a launch fails.
+ * Advance nsteps >= 0 time steps (Eq. 1).  All the steps run in one
+ * persistent launch of the fused kernel (more than one only when nsteps x
+ * warp tiles exceeds 2^30): a warp tile of step t + 1 starts once the tiles
+ * around it have finished step t.  The result is bit for bit that of nsteps
+ * one-step calls.  Asynchronous; returns LBM_ERR_CUDA if a launch fails.  A
+ * wait that runs out (it cannot in a correct launch; it is bounded all the
+ * same) raises LBM_STATUS_TIMEOUT (see lbm_check) and ends the launch early.
  */
 LBM_API int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream);
 
@@ -265,8 +270,8 @@ LBM_API int lbm_get_launch(const lbm_lattice *h, int32_t *band_rows, int32_t *wa
 
 /*
  * Batches: independent lattices of any sizes (one storage type) stepped
- * together, one launch per step over all members (every member advances
- * exactly as it would alone under Eq. 1).
+ * together, all members' warp tiles in one persistent launch of many steps
+ * (every member advances exactly as it would alone under Eq. 1).
  *   lbm_batch_create   empty batch for lattices of the given lbm_storage.
  *   lbm_batch_add / lbm_batch_remove
  *                      change the membership (takes effect at the next
@@ -276,9 +281,10 @@ LBM_API int lbm_get_launch(const lbm_lattice *h, int32_t *band_rows, int32_t *wa
  *                      tables and step counter; lbm_get_fields and friends
  *                      work on members as usual.
  *   lbm_batch_step     nsteps steps of every member on the stream; with
- *                      use_graph != 0, whole chunks of 16 steps are replayed
- *                      from a captured CUDA graph (re-captured when the
- *                      membership or a member's parameters change).
+ *                      use_graph != 0, whole chunks of 64 steps are replayed
+ *                      from a captured CUDA graph of one launch (re-captured
+ *                      when the membership or a member's parameters
+ *                      change), the rest runs as one launch.
  *   lbm_batch_set_launch / lbm_batch_get_launch
  *                      launch shape shared by all members (as lbm_set_launch;
  *                      tiles = warp tiles per step).

@@ -162,9 +162,11 @@ struct lbm_batch {
     size_t cap_params;
     lbm::TileRef *d_tiles;
     size_t cap_tiles;
+    unsigned *d_sync;  // multi-step launch: work counter, then one counter per table entry (cap_tiles + 1)
     int ntiles;
     int band, warps, band_eff;
     int sms;
+    int ctas_max;  // CTAs resident on the device at once (persistent grid)
     cudaStream_t capture;  // private stream used to capture step graphs
     cudaGraphExec_t graph;
     int graph_version, graph_steps;
@@ -321,7 +323,7 @@ bool valid(const lbm_lattice *h) { return h != nullptr && h->mem != nullptr; }
 // ---- batches ------------------------------------------------------------------------
 namespace {
 
-constexpr int kGraphSteps = 16;  // steps per captured graph of a batch
+constexpr int kGraphSteps = 64;  // steps of the one launch a captured batch graph holds
 
 size_t params_size(int storage)
 {
@@ -402,9 +404,14 @@ int batch_rebuild(lbm_batch *b, cudaStream_t s)
         }
         if (e == cudaSuccess && tiles.size() > b->cap_tiles) {
             cudaFree(b->d_tiles);
+            cudaFree(b->d_sync);
             b->d_tiles = nullptr;
-            e = cudaMalloc(&b->d_tiles, std::max<size_t>(1, tiles.size() * 2) * sizeof(lbm::TileRef));
-            b->cap_tiles = e == cudaSuccess ? tiles.size() * 2 : 0;
+            b->d_sync = nullptr;
+            const size_t cap = std::max<size_t>(1, tiles.size() * 2);
+            e = cudaMalloc(&b->d_tiles, cap * sizeof(lbm::TileRef));
+            if (e == cudaSuccess)
+                e = cudaMalloc(&b->d_sync, (cap + 1) * sizeof(unsigned));
+            b->cap_tiles = e == cudaSuccess ? cap : 0;
         }
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -418,40 +425,59 @@ int batch_rebuild(lbm_batch *b, cudaStream_t s)
     if (e != cudaSuccess)
         return cuda_fail(e, "batch table upload");
     b->ntiles = (int)tiles.size();
+    b->ctas_max = per_sm * std::max(1, b->sms);
     b->dirty = false;
     b->version += 1;
     return LBM_OK;
 }
 
-cudaError_t batch_launch(lbm_batch *b, cudaStream_t s)
+// nsteps steps of every member in one persistent launch (counters zeroed first)
+cudaError_t batch_launch(lbm_batch *b, int nsteps, cudaStream_t s)
 {
     const int n = (int)b->members.size();
+    cudaError_t e = cudaMemsetAsync(b->d_sync, 0, (size_t)(b->ntiles + 1) * sizeof(unsigned), s);
+    if (e != cudaSuccess)
+        return e;
+    lbm::RunCtl ctl;
+    ctl.counter = b->d_sync;
+    ctl.flags = b->d_sync + 1;
+    ctl.nsteps = nsteps;
+    ctl.radius = b->band_eff >= 2 ? 1 : 2;
+    ctl.wrap = 0;  // read from each lattice's parameters
+    const int ctas = (int)std::min<int64_t>(b->ctas_max, ((int64_t)nsteps * b->ntiles + b->warps - 1) / b->warps);
     switch (b->storage) {
     case LBM_F64:
         return lbm::launch_batch_f64(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<double> *>(b->d_params), n,
-                                     b->warps, s);
+                                     ctl, b->warps, ctas, s);
     case LBM_F32:
         return lbm::launch_batch_f32(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params), n,
-                                     b->warps, s);
+                                     ctl, b->warps, ctas, s);
     case LBM_F16:
         return lbm::launch_batch_f16(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params), n,
-                                     b->warps, s);
+                                     ctl, b->warps, ctas, s);
     default:
         return lbm::launch_batch_bf16(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params), n,
-                                      b->warps, s);
+                                      ctl, b->warps, ctas, s);
     }
 }
 
-// instantiate (once per table version) a graph of kGraphSteps batch steps
+// steps per batch launch: the work counter stays below 2^31
+int64_t batch_steps_per_launch(const lbm_batch *b)
+{
+    return std::max<int64_t>(1, ((int64_t)1 << 31) / std::max<int64_t>(1, 2 * (int64_t)b->ntiles));
+}
+
+// instantiate (once per table version) a graph of one launch of kGraphSteps steps
 int batch_graph(lbm_batch *b)
 {
     if (b->graph && b->graph_version == b->version)
         return LBM_OK;
     drop_graph(b);
     cudaGraph_t g = nullptr;
+    const int steps = (int)std::min<int64_t>(kGraphSteps, batch_steps_per_launch(b));
     cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
-    for (int k = 0; e == cudaSuccess && k < kGraphSteps; ++k)
-        e = batch_launch(b, b->capture);
+    if (e == cudaSuccess)
+        e = batch_launch(b, steps, b->capture);
     cudaError_t e2 = cudaStreamEndCapture(b->capture, &g);
     if (e == cudaSuccess)
         e = e2;
@@ -465,7 +491,7 @@ int batch_graph(lbm_batch *b)
         return cuda_fail(e, "capturing the batch step graph");
     }
     b->graph_version = b->version;
-    b->graph_steps = kGraphSteps;
+    b->graph_steps = steps;
     return LBM_OK;
 }
 
@@ -926,6 +952,7 @@ void lbm_batch_destroy(lbm_batch *b)
     drop_graph(b);
     cudaFree(b->d_params);
     cudaFree(b->d_tiles);
+    cudaFree(b->d_sync);
     cudaStreamDestroy(b->capture);
     delete b;
 }
@@ -997,7 +1024,7 @@ int lbm_batch_step(lbm_batch *b, int32_t nsteps, int32_t use_graph, lbm_stream s
             return rc;
     }
     int done = 0;
-    if (use_graph && nsteps >= kGraphSteps) {
+    if (use_graph) {
         int rc = batch_graph(b);
         if (rc)
             return rc;
@@ -1009,12 +1036,14 @@ int lbm_batch_step(lbm_batch *b, int32_t nsteps, int32_t use_graph, lbm_stream s
             }
         }
     }
-    for (; done < nsteps; ++done) {
-        cudaError_t e = batch_launch(b, s);
+    while (done < nsteps) {
+        const int m = (int)std::min<int64_t>(batch_steps_per_launch(b), nsteps - done);
+        cudaError_t e = batch_launch(b, m, s);
         if (e != cudaSuccess) {
             batch_advance_host(b, done);
             return cuda_fail(e, "batch step launch");
         }
+        done += m;
     }
     batch_advance_host(b, nsteps);
     return LBM_OK;

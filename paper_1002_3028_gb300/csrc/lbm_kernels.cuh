@@ -859,7 +859,7 @@ struct RunCtl {
     unsigned *flags;    // per warp tile: 32 x sub-steps done (zeroed before the launch)
     int nsteps;         // sub-steps of this launch
     int radius;         // neighbour bands a tile depends on
-    int wrap;           // strips wrap around (periodic axial ends)
+    int wrap;           // strips wrap around (periodic axial ends; a batch reads each lattice's ends)
 };
 
 __device__ __forceinline__ unsigned ld_relaxed(const unsigned *a)
@@ -880,25 +880,25 @@ __device__ __forceinline__ void red_release_add(unsigned *a, unsigned v)
 // semantics.  Returns false if the wait runs out or another warp's wait ran
 // out (the status word is read only while waiting).
 template <class C>
-__device__ bool wait_neighbours(const StepParams<C> &p, const RunCtl &ctl, int tile, int k)
+__device__ bool wait_neighbours(const StepParams<C> &p, const unsigned *flags, int radius, bool wrap, int tile, int k)
 {
     const int s = tile % p.nstrips, b = tile / p.nstrips;
     const int nbands = (p.nr + p.band - 1) / p.band;
     const unsigned want = 32u * (unsigned)k;
     for (int it = 0;; ++it) {
         bool ok = true;
-        for (int db = -ctl.radius; db <= ctl.radius; ++db) {
+        for (int db = -radius; db <= radius; ++db) {
             const int bb = b + db;
             if (bb < 0 || bb >= nbands)
                 continue;
 #pragma unroll
             for (int ds = -1; ds <= 1; ++ds) {
                 int ss = s + ds;
-                if (ctl.wrap)
+                if (wrap)
                     ss = ss < 0 ? ss + p.nstrips : (ss >= p.nstrips ? ss - p.nstrips : ss);
                 if (ss < 0 || ss >= p.nstrips)
                     continue;
-                ok &= (int)(ld_relaxed(ctl.flags + bb * p.nstrips + ss) - want) >= 0;
+                ok &= (int)(ld_relaxed(flags + bb * p.nstrips + ss) - want) >= 0;
             }
         }
         if (__all_sync(0xffffffffu, ok)) {
@@ -932,7 +932,7 @@ __global__ void __launch_bounds__(256) step_run_kernel(const __grid_constant__ S
             next = atomicAdd(ctl.counter, 1u);
         const int k = (int)(n / (unsigned)p.ntiles);
         const int tile = (int)(n - (unsigned)k * (unsigned)p.ntiles);
-        if (k > 0 && !wait_neighbours<C>(p, ctl, tile, k)) {
+        if (k > 0 && !wait_neighbours<C>(p, ctl.flags, ctl.radius, ctl.wrap != 0, tile, k)) {
             if (lane == 0)
                 atomicOr(p.status, STATUS_TIMEOUT);
             break;  // whole warp
@@ -946,20 +946,24 @@ __global__ void __launch_bounds__(256) step_run_kernel(const __grid_constant__ S
 }
 
 // ---- many lattices in one launch --------------------------------------------------------
-// A batch of independent lattices of any sizes (same storage type) steps in
-// one launch: a table lists every warp tile as (lattice, tile of that
-// lattice); each warp copies its lattice's parameters from the batch's
-// parameter table into shared memory and runs the same tile code.  The
-// parameters (buffers, step counter) advance on the device after each step
-// (advance_kernel), so a captured sequence of steps can be replayed.
+// A batch of independent lattices of any sizes (same storage type) runs
+// many steps in one persistent launch, exactly like one lattice: a table
+// lists every warp tile of every member as (lattice, tile of that lattice),
+// and work item n of a launch is sub-step n / T (T table entries) of entry
+// n % T.  Each entry has its own completion counter; the counters of one
+// lattice are consecutive (its entries are), so a tile finds its
+// neighbours' counters from its own entry index.  Each warp copies its
+// lattice's parameters from the batch's parameter table into shared memory.
+// After the launch the parameters (buffers, step counter) advance on the
+// device (advance_kernel), so a captured launch can be replayed.
 struct TileRef {
     int lattice;  // index in the batch's parameter table
     int tile;     // warp tile index within that lattice
 };
 
 template <class S, class C>
-__global__ void __launch_bounds__(256) batch_step_kernel(const TileRef *__restrict__ tiles, int ntiles,
-                                                         const StepParams<C> *__restrict__ lattices)
+__global__ void __launch_bounds__(256) batch_run_kernel(const TileRef *__restrict__ tiles, int ntiles,
+                                                        const StepParams<C> *__restrict__ lattices, const RunCtl ctl)
 {
     constexpr int NV = NodesPerLane<C>::value;
     constexpr int PW = (int)((sizeof(StepParams<C>) + 15) / 16);  // 16-byte words per parameter block
@@ -967,19 +971,38 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const TileRef *__restri
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpc = blockDim.x >> 5;
-    const int idx = blockIdx.x * wpc + warp;
-    if (idx >= ntiles)
-        return;  // whole warp
-    const TileRef t = tiles[idx];
     // parameter blocks of all warps first, then the warps' staging rings
     StepParams<C> *pw = reinterpret_cast<StepParams<C> *>(smem_raw) + warp;
-    static_assert(sizeof(StepParams<C>) % 16 == 0 && PW <= 32, "parameter block copy");
-    if (lane < PW)
-        reinterpret_cast<uint4 *>(pw)[lane] = reinterpret_cast<const uint4 *>(lattices + t.lattice)[lane];
-    __syncwarp();
-    const StepParams<C> &p = *pw;
     S *wsm = reinterpret_cast<S *>(smem_raw + wpc * sizeof(StepParams<C>)) + (size_t)warp * Stages<NV>::value * Win<S, NV>::STAGE;
-    step_tile<S, NV, C>(p, static_cast<const S *>(p.src), static_cast<S *>(p.dst), wsm, t.tile, lane, p.step);
+    static_assert(sizeof(StepParams<C>) % 16 == 0 && PW <= 32, "parameter block copy");
+    const unsigned total = (unsigned)ctl.nsteps * (unsigned)ntiles;
+    unsigned n = 0;
+    if (lane == 0)
+        n = atomicAdd(ctl.counter, 1u);
+    n = __shfl_sync(0xffffffffu, n, 0);
+    while (n < total) {
+        unsigned next = 0;
+        if (lane == 0)
+            next = atomicAdd(ctl.counter, 1u);
+        const int k = (int)(n / (unsigned)ntiles);
+        const int idx = (int)(n - (unsigned)k * (unsigned)ntiles);
+        const TileRef t = tiles[idx];
+        __syncwarp();  // every lane is done with the previous parameter block
+        if (lane < PW)
+            reinterpret_cast<uint4 *>(pw)[lane] = reinterpret_cast<const uint4 *>(lattices + t.lattice)[lane];
+        __syncwarp();
+        const StepParams<C> &p = *pw;
+        if (k > 0 && !wait_neighbours<C>(p, ctl.flags + (idx - t.tile), ctl.radius, p.bc_in == IN_PERIODIC, t.tile, k)) {
+            if (lane == 0)
+                atomicOr(p.status, STATUS_TIMEOUT);
+            break;  // whole warp
+        }
+        const S *src = static_cast<const S *>((k & 1) ? p.dst : p.src);
+        S *dst = static_cast<S *>((k & 1) ? const_cast<void *>(p.src) : p.dst);
+        step_tile<S, NV, C>(p, src, dst, wsm, t.tile, lane, p.step + k);
+        red_release_add(ctl.flags + idx, 1u);
+        n = __shfl_sync(0xffffffffu, next, 0);
+    }
 }
 
 template <class S, class C>
@@ -988,18 +1011,21 @@ constexpr int batch_smem_per_warp()
     return step_smem_per_warp<S, C>() + (int)sizeof(StepParams<C>);
 }
 
-// after a batch step: every lattice swaps its buffers and counts the step
+// after a batch launch of nsteps steps: every lattice counts the steps and,
+// for an odd count, swaps its buffers
 template <class C>
-__global__ void advance_kernel(StepParams<C> *lattices, int n)
+__global__ void advance_kernel(StepParams<C> *lattices, int n, int nsteps)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n)
         return;
     StepParams<C> &p = lattices[m];
-    const void *s = p.src;
-    p.src = p.dst;
-    p.dst = const_cast<void *>(s);
-    p.step += 1;
+    if (nsteps & 1) {
+        const void *s = p.src;
+        p.src = p.dst;
+        p.dst = const_cast<void *>(s);
+    }
+    p.step += nsteps;
 }
 
 // ---- ghosts of a stored state (after it is set from outside) ------------------------

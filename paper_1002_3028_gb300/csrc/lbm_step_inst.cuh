@@ -30,30 +30,30 @@ cudaError_t LBM_CAT(occupancy_run_, LBM_TAG)(int warps_per_cta, int *ctas_per_sm
                                                          warps_per_cta * step_smem_per_warp<LBM_S, LBM_C>());
 }
 
-// one batch step (all member lattices) followed by the device-side advance
+// nsteps steps of every member lattice in one persistent launch, then the
+// device-side advance of the parameter table
 cudaError_t LBM_CAT(launch_batch_, LBM_TAG)(const TileRef *tiles, int ntiles, StepParams<LBM_C> *lattices, int nlat,
-                                            int warps_per_cta, cudaStream_t s)
+                                            const RunCtl &ctl, int warps_per_cta, int ctas, cudaStream_t s)
 {
-    if (ntiles <= 0 || nlat <= 0)
+    if (ntiles <= 0 || nlat <= 0 || ctl.nsteps <= 0)
         return cudaSuccess;
     const int smem = warps_per_cta * batch_smem_per_warp<LBM_S, LBM_C>();
-    const int ctas = (ntiles + warps_per_cta - 1) / warps_per_cta;
-    batch_step_kernel<LBM_S, LBM_C><<<ctas, 32 * warps_per_cta, smem, s>>>(tiles, ntiles, lattices);
+    batch_run_kernel<LBM_S, LBM_C><<<ctas, 32 * warps_per_cta, smem, s>>>(tiles, ntiles, lattices, ctl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    advance_kernel<LBM_C><<<(nlat + 127) / 128, 128, 0, s>>>(lattices, nlat);
+    advance_kernel<LBM_C><<<(nlat + 127) / 128, 128, 0, s>>>(lattices, nlat, ctl.nsteps);
     return cudaGetLastError();
 }
 
 cudaError_t LBM_CAT(occupancy_batch_, LBM_TAG)(int warps_per_cta, int *ctas_per_sm)
 {
-    cudaError_t e = cudaFuncSetAttribute(batch_step_kernel<LBM_S, LBM_C>,
+    cudaError_t e = cudaFuncSetAttribute(batch_run_kernel<LBM_S, LBM_C>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          8 * batch_smem_per_warp<LBM_S, LBM_C>());
     if (e != cudaSuccess)
         return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, batch_step_kernel<LBM_S, LBM_C>,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, batch_run_kernel<LBM_S, LBM_C>,
                                                          32 * warps_per_cta,
                                                          warps_per_cta * batch_smem_per_warp<LBM_S, LBM_C>());
 }

@@ -314,7 +314,7 @@ class Lattice:
 
 
 class Batch:
-    """Independent lattices of one storage type stepped together, one launch per step."""
+    """Independent lattices of one storage type stepped together in persistent multi-step launches."""
 
     def __init__(self, storage: str = "f16"):
         if storage not in STORAGE:

@@ -3,8 +3,8 @@
 Requests (a lattice, its inlet and tables, a step count) arrive over time.
 The scheduler admits them first-in first-out as long as their device memory
 fits the HBM budget, keeps every admitted lattice resident on the GPU, and
-advances all active lattices together as one batch (one launch per step for
-all of them), in chunks that end where the next active request completes.
+advances all active lattices together as one batch (one persistent launch
+for many steps of all of them), in chunks that end where the next active request completes.
 A finished request leaves the batch at once; its fields are copied to pinned
 host memory asynchronously and its memory is released when that copy has
 landed, so requests that arrive while others run are admitted as soon as
@@ -136,7 +136,7 @@ def serve(requests: List[Request], engine: Engine, budget_bytes: float, chunk: i
 
 
 class GpuBatchEngine(Engine):
-    """All active lattices in one liblbm batch (one launch per step, graph replay)."""
+    """All active lattices in one liblbm batch (persistent multi-step launches, graph replay)."""
 
     def __init__(self, storage: str = "f16", device=None, graph: bool = True):
         import torch
