@@ -268,6 +268,13 @@ LBM_API int lbm_set_launch(lbm_lattice *h, int32_t band_rows, int32_t warps_per_
  * launch (any pointer may be NULL). */
 LBM_API int lbm_get_launch(const lbm_lattice *h, int32_t *band_rows, int32_t *warps_per_cta, int32_t *ctas);
 
+/* Work-item size of lbm_step's persistent launch: a warp takes `group`
+ * adjacent warp tiles of one band at a time and synchronises with its
+ * neighbours once per item (1..64; 0 = automatic).  Results do not depend
+ * on it.  lbm_get_item_group returns the value in use (-1 for a bad handle). */
+LBM_API int lbm_set_item_group(lbm_lattice *h, int32_t group);
+LBM_API int32_t lbm_get_item_group(const lbm_lattice *h);
+
 /*
  * Batches: independent lattices of any sizes (one storage type) stepped
  * together, all members' warp tiles in one persistent launch of many steps

@@ -147,6 +147,7 @@ struct lbm_lattice {
     int band, warps;       // launch shape; band 0 = chosen from the occupancy
     int band_eff, ctas;    // band and CTA count of a one-step lbm_step launch
     int ctas_max;          // CTAs resident on the device at once (persistent grid)
+    int group;             // warp tiles per work item of lbm_step (0 = automatic)
     int device, sms;
 
     void *buf(int b) const { return mem + L.off_buf[b]; }
@@ -229,12 +230,17 @@ lbm::StepParams<float> params_f(const lbm_lattice *h)
                               h->at<float>(h->L.off_nu_f), h->at<float>(h->L.off_al_f));
 }
 
-// Launch shape of the step kernel: one warp per strip x band-row tile, all
-// tiles in one grid, one warp per CTA by default.  The automatic band height
-// keeps about five tiles per resident warp (so CTAs start and finish at
-// staggered times and the last wave is short), bounded to 4..16 rows (each
-// band pulls two extra halo rows).  Measured on the 4096 x 1024 jet, this
-// picks band 6, the fastest of bands 4..64 for FP32 and FP16 storage.
+// warp tiles per work item of lbm_step: the set value, else 1
+int item_group(const lbm_lattice *h) { return h->group > 0 ? h->group : 1; }
+
+// Launch shape of the step kernel: a persistent grid of one-warp CTAs (by
+// default) working through strip x band tiles.  A tile of step t + 1 waits
+// for the tiles around it of step t, which precede it by one step's worth
+// of tiles in the work order; the automatic band height keeps that distance
+// at about 4.5 rounds of the resident warps (3.4 for 2-byte storage), which
+// leaves the waits rare, with bands of 4..8 rows (each band stages two halo
+// rows).  On the 4096 x 1024 jet this picks band 6 for FP32 and band 8 for
+// FP16 storage, the fastest of bands 4..10 measured for each.
 int plan_launch(lbm_lattice *h)
 {
     int per_sm = 0;
@@ -254,9 +260,10 @@ int plan_launch(lbm_lattice *h)
     if (h->band > 0) {
         h->band_eff = h->band;
     } else {
-        const int64_t want_tiles = 5 * (int64_t)resident_warps;
-        const int64_t band = ((int64_t)h->d.nr * nstrips + want_tiles - 1) / want_tiles;
-        h->band_eff = (int)std::min<int64_t>(16, std::max<int64_t>(4, band));
+        const int64_t rounds10 = storage_bytes(h->d.storage) == 2 ? 34 : 45;  // tenths of a round
+        const int64_t want_tiles = std::max<int64_t>(1, rounds10 * resident_warps / 10);
+        const int64_t band = ((int64_t)h->d.nr * nstrips + want_tiles / 2) / want_tiles;
+        h->band_eff = (int)std::min<int64_t>(8, std::max<int64_t>(4, band));
     }
     const int64_t ntiles = (int64_t)nstrips * ((h->d.nr + h->band_eff - 1) / h->band_eff);
     h->ctas_max = per_sm * std::max(1, h->sms);
@@ -590,6 +597,7 @@ int lbm_create(const lbm_desc *d, void *dev_mem, size_t bytes, lbm_lattice **out
     h->step = 0;
     h->band = 0;
     h->warps = 1;
+    h->group = 0;
     cudaGetDevice(&h->device);
     h->sms = 1;
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -712,23 +720,24 @@ int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
         return fail(LBM_ERR_INVALID_ARG, "the lattice belongs to a batch: step the batch");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const lbm_desc &d = h->d;
-    const int nstrips = (d.nx + strip_cols(d.storage) - 1) / strip_cols(d.storage);
-    const int64_t ntiles = (int64_t)nstrips * ((d.nr + h->band_eff - 1) / h->band_eff);
-    // steps per launch: the work counter stays below 2^31
-    const int64_t per_launch = std::max<int64_t>(1, ((int64_t)1 << 31) / std::max<int64_t>(1, 2 * ntiles));
-    unsigned *sync = h->at<unsigned>(h->L.off_sync);
     lbm::RunCtl ctl;
+    ctl.group = item_group(h);
+    const int nstrips = (d.nx + strip_cols(d.storage) - 1) / strip_cols(d.storage);
+    const int64_t items = (int64_t)lbm::item_cols(nstrips, ctl.group) * ((d.nr + h->band_eff - 1) / h->band_eff);
+    // steps per launch: the work counter stays below 2^31
+    const int64_t per_launch = std::max<int64_t>(1, ((int64_t)1 << 31) / std::max<int64_t>(1, 2 * items));
+    unsigned *sync = h->at<unsigned>(h->L.off_sync);
     ctl.counter = sync;
     ctl.flags = sync + 1;
     ctl.radius = h->band_eff >= 2 ? 1 : 2;
     ctl.wrap = d.bc_in == LBM_IN_PERIODIC ? 1 : 0;
     for (int64_t done = 0; done < nsteps;) {
         const int m = (int)std::min<int64_t>(per_launch, nsteps - done);
-        cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)4 * (size_t)(1 + ntiles), s);
+        cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)4 * (size_t)(1 + items), s);
         if (e != cudaSuccess)
             return cuda_fail(e, "work counter reset");
         ctl.nsteps = m;
-        const int ctas = (int)std::min<int64_t>(h->ctas_max, (m * ntiles + h->warps - 1) / h->warps);
+        const int ctas = (int)std::min<int64_t>(h->ctas_max, (m * items + h->warps - 1) / h->warps);
         switch (d.storage) {
         case LBM_F64: e = lbm::launch_run_f64(params_d(h), ctl, h->warps, ctas, s); break;
         case LBM_F32: e = lbm::launch_run_f32(params_f(h), ctl, h->warps, ctas, s); break;
@@ -744,6 +753,16 @@ int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
     }
     return LBM_OK;
 }
+
+int lbm_set_item_group(lbm_lattice *h, int32_t group)
+{
+    if (!valid(h) || group < 0 || group > 64)
+        return fail(LBM_ERR_INVALID_ARG, "bad handle or group (0..64)");
+    h->group = group;
+    return LBM_OK;
+}
+
+int32_t lbm_get_item_group(const lbm_lattice *h) { return valid(h) ? item_group(h) : -1; }
 
 int64_t lbm_get_step(const lbm_lattice *h) { return valid(h) ? h->step : -1; }
 

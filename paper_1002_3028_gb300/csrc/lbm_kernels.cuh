@@ -835,37 +835,44 @@ constexpr int step_smem_per_warp()
 }
 
 // ---- many steps of one lattice in one launch ----------------------------------------
-// lbm_step runs all its steps in one persistent launch.  Warps take warp
-// tiles from a counter in step-major order (work item n = k * ntiles + tile
-// for sub-step k).  A tile of sub-step k > 0 reads what the tiles around it
-// wrote in sub-step k - 1 and overwrites what they read there: rows within
-// one band (two bands for one-row bands) and columns within one strip
+// lbm_step runs all its steps in one persistent launch.  A work item is a
+// group of G adjacent warp tiles of one band (strips g G .. g G + G - 1);
+// warps take items from a counter in step-major order (item n = k * items
+// + i for sub-step k) and run the group's tiles one after the other.  An
+// item of sub-step k > 0 reads what the items around it wrote in sub-step
+// k - 1 and overwrites what they read there: rows within one band (two
+// bands for one-row bands) and columns within one strip beyond the group
 // (wrapping around for periodic ends).  So before starting it waits until
-// those neighbour tiles count sub-step k - 1 as done.  Each lane adds one
-// to its tile's counter with release semantics after its last store, so a
-// tile is done with sub-step k - 1 once its counter reaches 32 k; the
-// waiting lanes each read every neighbour counter, then fence (acquire).
-// Every neighbour's work item precedes the waiting one in the counter
+// those neighbour items count sub-step k - 1 as done.  Each lane adds one
+// to its item's counter with release semantics after its last store, so an
+// item is done with sub-step k - 1 once its counter reaches 32 k.  To wait,
+// lane l watches one neighbour counter with acquire loads; a warp barrier
+// (which orders memory among its lanes) then hands the acquired view to
+// every lane.  Every neighbour item precedes the waiting one in the counter
 // order, so it was taken by a warp that is already running; a warp works on
 // its items in counter order, and the lowest unfinished item never waits on
-// a later one, so the waits end.  Each wait is bounded all the
-// same; a wait that runs out raises LBM_STATUS_TIMEOUT in the lattice's
-// status word and every warp stops taking work.
+// a later one, so the waits end.  Each wait is bounded all the same; a
+// wait that runs out raises LBM_STATUS_TIMEOUT in the lattice's status
+// word and the warps stop taking work.
 constexpr int STATUS_TIMEOUT = 1;
 constexpr int RUN_SPIN_LIMIT = 1 << 22;  // polls of at most ~1 us: a few seconds
 
 struct RunCtl {
     unsigned *counter;  // work items taken (zeroed before the launch)
-    unsigned *flags;    // per warp tile: 32 x sub-steps done (zeroed before the launch)
+    unsigned *flags;    // per work item: 32 x sub-steps done (zeroed before the launch)
     int nsteps;         // sub-steps of this launch
-    int radius;         // neighbour bands a tile depends on
+    int radius;         // neighbour bands an item depends on
     int wrap;           // strips wrap around (periodic axial ends; a batch reads each lattice's ends)
+    int group;          // G: warp tiles (adjacent strips of one band) per work item
 };
 
-__device__ __forceinline__ unsigned ld_relaxed(const unsigned *a)
+// work items per band of a lattice with nstrips strips
+__host__ __device__ __forceinline__ int item_cols(int nstrips, int group) { return (nstrips + group - 1) / group; }
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *a)
 {
     unsigned v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(a) : "memory");
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(a) : "memory");
     return v;
 }
 
@@ -874,35 +881,31 @@ __device__ __forceinline__ void red_release_add(unsigned *a, unsigned v)
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;\n" ::"l"(a), "r"(v) : "memory");
 }
 
-// Every lane waits until the tiles around `tile` have finished sub-step
-// k - 1: the counters are polled with relaxed loads (all in flight at once)
-// and, once every one is high enough, a fence gives the polls acquire
-// semantics.  Returns false if the wait runs out or another warp's wait ran
-// out (the status word is read only while waiting).
+// Every lane waits until the items around item (band b, column g) of a
+// lattice (its counters start at `flags`, `cols` items per band) have
+// finished sub-step k - 1.  Returns false if the wait runs out or another
+// warp's wait ran out (the status word is read only while waiting).
 template <class C>
-__device__ bool wait_neighbours(const StepParams<C> &p, const unsigned *flags, int radius, bool wrap, int tile, int k)
+__device__ bool wait_neighbours(const StepParams<C> &p, const unsigned *flags, int cols, int radius, bool wrap, int b,
+                                int g, int k)
 {
-    const int s = tile % p.nstrips, b = tile / p.nstrips;
+    // lane l < 3 (2 radius + 1) watches neighbour (band b + l / 3 - radius, column g + l % 3 - 1)
     const int nbands = (p.nr + p.band - 1) / p.band;
+    const int lane = threadIdx.x & 31;
+    const unsigned *f = nullptr;
+    if (lane < 3 * (2 * radius + 1)) {
+        const int bb = b + lane / 3 - radius;
+        int gg = g + lane % 3 - 1;
+        if (wrap)
+            gg = gg < 0 ? gg + cols : (gg >= cols ? gg - cols : gg);
+        if (bb >= 0 && bb < nbands && gg >= 0 && gg < cols)
+            f = flags + bb * cols + gg;
+    }
     const unsigned want = 32u * (unsigned)k;
     for (int it = 0;; ++it) {
-        bool ok = true;
-        for (int db = -radius; db <= radius; ++db) {
-            const int bb = b + db;
-            if (bb < 0 || bb >= nbands)
-                continue;
-#pragma unroll
-            for (int ds = -1; ds <= 1; ++ds) {
-                int ss = s + ds;
-                if (wrap)
-                    ss = ss < 0 ? ss + p.nstrips : (ss >= p.nstrips ? ss - p.nstrips : ss);
-                if (ss < 0 || ss >= p.nstrips)
-                    continue;
-                ok &= (int)(ld_relaxed(flags + bb * p.nstrips + ss) - want) >= 0;
-            }
-        }
+        const bool ok = f == nullptr || (int)(ld_acquire(f) - want) >= 0;
         if (__all_sync(0xffffffffu, ok)) {
-            __threadfence();
+            __syncwarp();  // orders memory among the lanes: every lane now sees what its watcher acquired
             return true;
         }
         if (it >= RUN_SPIN_LIMIT || (*static_cast<volatile int *>(p.status) & STATUS_TIMEOUT))
@@ -919,28 +922,32 @@ __global__ void __launch_bounds__(256) step_run_kernel(const __grid_constant__ S
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     S *wsm = reinterpret_cast<S *>(smem_raw) + (size_t)warp * Stages<NV>::value * Win<S, NV>::STAGE;
-    const unsigned total = (unsigned)ctl.nsteps * (unsigned)p.ntiles;
+    const int cols = item_cols(p.nstrips, ctl.group);
+    const unsigned items = (unsigned)cols * (unsigned)((p.nr + p.band - 1) / p.band);
+    const unsigned total = (unsigned)ctl.nsteps * items;
     unsigned n = 0;
     if (lane == 0)
         n = atomicAdd(ctl.counter, 1u);
     n = __shfl_sync(0xffffffffu, n, 0);
     while (n < total) {
-        // take the next work item now: its latency hides behind this tile
-        // (items are still started in counter order by each warp)
+        // take the next item now: its latency hides behind this one
         unsigned next = 0;
         if (lane == 0)
             next = atomicAdd(ctl.counter, 1u);
-        const int k = (int)(n / (unsigned)p.ntiles);
-        const int tile = (int)(n - (unsigned)k * (unsigned)p.ntiles);
-        if (k > 0 && !wait_neighbours<C>(p, ctl.flags, ctl.radius, ctl.wrap != 0, tile, k)) {
+        const int k = (int)(n / items);
+        const int item = (int)(n - (unsigned)k * items);
+        const int b = item / cols, g = item - b * cols;
+        if (k > 0 && !wait_neighbours<C>(p, ctl.flags, cols, ctl.radius, ctl.wrap != 0, b, g, k)) {
             if (lane == 0)
                 atomicOr(p.status, STATUS_TIMEOUT);
             break;  // whole warp
         }
         const S *src = static_cast<const S *>((k & 1) ? p.dst : p.src);
         S *dst = static_cast<S *>((k & 1) ? const_cast<void *>(p.src) : p.dst);
-        step_tile<S, NV, C>(p, src, dst, wsm, tile, lane, p.step + k);
-        red_release_add(ctl.flags + tile, 1u);
+        const int s1 = min((g + 1) * ctl.group, p.nstrips);
+        for (int s = g * ctl.group; s < s1; ++s)
+            step_tile<S, NV, C>(p, src, dst, wsm, b * p.nstrips + s, lane, p.step + k);
+        red_release_add(ctl.flags + item, 1u);
         n = __shfl_sync(0xffffffffu, next, 0);
     }
 }
@@ -992,7 +999,8 @@ __global__ void __launch_bounds__(256) batch_run_kernel(const TileRef *__restric
             reinterpret_cast<uint4 *>(pw)[lane] = reinterpret_cast<const uint4 *>(lattices + t.lattice)[lane];
         __syncwarp();
         const StepParams<C> &p = *pw;
-        if (k > 0 && !wait_neighbours<C>(p, ctl.flags + (idx - t.tile), ctl.radius, p.bc_in == IN_PERIODIC, t.tile, k)) {
+        if (k > 0 && !wait_neighbours<C>(p, ctl.flags + (idx - t.tile), p.nstrips, ctl.radius, p.bc_in == IN_PERIODIC,
+                                         t.tile / p.nstrips, t.tile % p.nstrips, k)) {
             if (lane == 0)
                 atomicOr(p.status, STATUS_TIMEOUT);
             break;  // whole warp

@@ -108,6 +108,9 @@ def lib(build: bool = True):
             L.lbm_restore.argtypes = [vp, vp, i64, vp]
             L.lbm_set_launch.argtypes = [vp, i32, i32]
             L.lbm_get_launch.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+            L.lbm_set_item_group.argtypes = [vp, i32]
+            L.lbm_get_item_group.restype = i32
+            L.lbm_get_item_group.argtypes = [vp]
             L.lbm_check.argtypes = [vp, C.POINTER(i32)]
             L.lbm_diagnostics.argtypes = [vp, C.POINTER(Diag), vp]
             L.lbm_diagnostics_noalloc.argtypes = [vp, C.POINTER(Diag), vp]
@@ -216,6 +219,14 @@ class Lattice:
     def set_launch(self, band_rows: int = 0, warps_per_cta: int = 0):
         """band_rows 0 = automatic (one wave of resident warps); warps 0 = unchanged."""
         _check(self._L.lbm_set_launch(self._h, band_rows, warps_per_cta), "lbm_set_launch")
+
+    def set_item_group(self, group: int = 0):
+        """Warp tiles per work item of the persistent step launch (0 = automatic)."""
+        _check(self._L.lbm_set_item_group(self._h, int(group)), "lbm_set_item_group")
+
+    @property
+    def item_group(self) -> int:
+        return int(self._L.lbm_get_item_group(self._h))
 
     def launch(self):
         """(band rows, warps per CTA, CTAs) used by lbm_step."""

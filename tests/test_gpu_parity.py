@@ -228,20 +228,24 @@ def test_launch_shape_does_not_change_results(lbm, orc, band, warps):
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
 
 
-@pytest.mark.parametrize("storage,bounds,band", [
-    ("f32", "jet", 0), ("f32", "jet", 1), ("f32", "periodic_axis", 0), ("f32", "open_periodic", 1),
-    ("f16", "pipe", 4), ("f64", "jet", 0), ("f64", "annulus", 2),
+@pytest.mark.parametrize("storage,bounds,band,group", [
+    ("f32", "jet", 0, 1), ("f32", "jet", 1, 1), ("f32", "periodic_axis", 0, 1), ("f32", "open_periodic", 1, 1),
+    ("f16", "pipe", 4, 1), ("f64", "jet", 0, 1), ("f64", "annulus", 2, 1),
+    ("f32", "jet", 0, 2), ("f32", "periodic_axis", 4, 2), ("f32", "open_periodic", 1, 3), ("f64", "jet", 3, 4),
 ])
-def test_many_steps_in_one_launch_equal_single_steps(lbm, orc, storage, bounds, band):
-    """lbm_step(n) runs its n steps in one launch whose tiles wait for their neighbours of the
-    previous step; the result is bit for bit that of n separate one-step launches (one-row
-    bands depend on two bands each side; periodic ends make the first and last strips
-    neighbours).  The lattice spans several strips and bands with a ragged last strip."""
+def test_many_steps_in_one_launch_equal_single_steps(lbm, orc, storage, bounds, band, group):
+    """lbm_step(n) runs its n steps in one launch whose work items wait for their neighbours
+    of the previous step; the result is bit for bit that of n separate one-step launches
+    (one-row bands depend on two bands each side; periodic ends make the first and last
+    items neighbours; items of several strips, a ragged last one, or one item per band).
+    The lattice spans several strips and bands with a ragged last strip."""
     w = workload(150, 45, **BOUNDARIES[bounds])
     one = lbm.Lattice.from_workload(w, storage)
     many = lbm.Lattice.from_workload(w, storage)
     for lat in (one, many):
         lat.set_launch(band, 1)
+    many.set_item_group(group)
+    assert many.item_group == group
     f0, g0 = I.random_state(150, 45, orc.feq(1.0, 0.02, 0.0), orc.geq(1.2, 0.02, 0.0), 0.05, 21)
     for lat in (one, many):
         lat.set_state(f0, g0, 3)
