@@ -74,14 +74,15 @@ def kernel_hash() -> str:
 
 
 def ncu_traffic(storage: str, workload: str):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    or None if there is none for this storage/workload or the kernel changed since."""
+    """DRAM bytes per step of the step kernel (a launch holds K steps; per step, like
+    `achieved`) from the committed ncu summary, or None if there is none for this
+    storage/workload or the kernel source changed since."""
     path = os.path.join(ROOT, "profiles", f"step_kernel_{storage}_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    b = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
+    b = re.search(r"dram_bytes_per_step_full_size:\s*([0-9.eE+]+)", text)
     if not h or not b or h.group(1) != kernel_hash():
         return None
     return float(b.group(1))
@@ -339,7 +340,8 @@ def run_gpu(args):
                    "launch": dict(zip(("band_rows", "warps_per_cta", "ctas" if len(lats) == 1 else "tiles"),
                                       launch))},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic},
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                     "per": "step (the timed steps run in persistent launches of many steps)"},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": step_launches(lats, args.storage, launch, args.steps),
