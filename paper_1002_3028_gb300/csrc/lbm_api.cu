@@ -238,9 +238,13 @@ int item_group(const lbm_lattice *h) { return h->group > 0 ? h->group : 1; }
 // for the tiles around it of step t, which precede it by one step's worth
 // of tiles in the work order; the automatic band height keeps that distance
 // at about 4.5 rounds of the resident warps (3.4 for 2-byte storage), which
-// leaves the waits rare, with bands of 4..8 rows (each band stages two halo
+// leaves the waits rare, with bands of 1..8 rows (each band stages two halo
 // rows).  On the 4096 x 1024 jet this picks band 6 for FP32 and band 8 for
-// FP16 storage, the fastest of bands 4..10 measured for each.
+// FP16 storage, the fastest of bands 4..10 measured for each.  Lattices
+// with fewer tiles than that are bound by the latency of one tile per step
+// and get the shortest bands (1024 x 256: band 1, 2.3x faster than band 4).
+// The grid holds at most one step's worth of tiles: warps beyond that could
+// only wait.
 int plan_launch(lbm_lattice *h)
 {
     int per_sm = 0;
@@ -262,8 +266,8 @@ int plan_launch(lbm_lattice *h)
     } else {
         const int64_t rounds10 = storage_bytes(h->d.storage) == 2 ? 34 : 45;  // tenths of a round
         const int64_t want_tiles = std::max<int64_t>(1, rounds10 * resident_warps / 10);
-        const int64_t band = ((int64_t)h->d.nr * nstrips + want_tiles / 2) / want_tiles;
-        h->band_eff = (int)std::min<int64_t>(8, std::max<int64_t>(4, band));
+        const int64_t band = ((int64_t)h->d.nr * nstrips + want_tiles - 1) / want_tiles;
+        h->band_eff = (int)std::min<int64_t>(8, std::max<int64_t>(1, band));
     }
     const int64_t ntiles = (int64_t)nstrips * ((h->d.nr + h->band_eff - 1) / h->band_eff);
     h->ctas_max = per_sm * std::max(1, h->sms);
@@ -374,9 +378,12 @@ int batch_rebuild(lbm_batch *b, cudaStream_t s)
     if (b->band > 0) {
         b->band_eff = b->band;
     } else {
-        const int64_t want_tiles = 5 * (int64_t)per_sm * std::max(1, b->sms) * b->warps;
-        const int64_t band = (area + want_tiles - 1) / std::max<int64_t>(1, want_tiles);
-        b->band_eff = (int)std::min<int64_t>(16, std::max<int64_t>(4, band));
+        // as for one lattice (plan_launch), up to 16 rows: a batch's tiles of one step are
+        // spread over many lattices, and longer bands halve the halo cost of small ones
+        const int64_t rounds10 = storage_bytes(b->storage) == 2 ? 34 : 45;
+        const int64_t want_tiles = std::max<int64_t>(1, rounds10 * (int64_t)per_sm * std::max(1, b->sms) * b->warps / 10);
+        const int64_t band = (area + want_tiles - 1) / want_tiles;
+        b->band_eff = (int)std::min<int64_t>(16, std::max<int64_t>(1, band));
     }
     std::vector<lbm::TileRef> tiles;
     std::vector<unsigned char> params(params_size(b->storage) * (size_t)std::max(1, n));
@@ -451,7 +458,7 @@ cudaError_t batch_launch(lbm_batch *b, int nsteps, cudaStream_t s)
     ctl.nsteps = nsteps;
     ctl.radius = b->band_eff >= 2 ? 1 : 2;
     ctl.wrap = 0;  // read from each lattice's parameters
-    const int ctas = (int)std::min<int64_t>(b->ctas_max, ((int64_t)nsteps * b->ntiles + b->warps - 1) / b->warps);
+    const int ctas = (int)std::min<int64_t>(b->ctas_max, ((int64_t)b->ntiles + b->warps - 1) / b->warps);
     switch (b->storage) {
     case LBM_F64:
         return lbm::launch_batch_f64(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<double> *>(b->d_params), n,
@@ -737,7 +744,7 @@ int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
         if (e != cudaSuccess)
             return cuda_fail(e, "work counter reset");
         ctl.nsteps = m;
-        const int ctas = (int)std::min<int64_t>(h->ctas_max, (m * items + h->warps - 1) / h->warps);
+        const int ctas = (int)std::min<int64_t>(h->ctas_max, (items + h->warps - 1) / h->warps);
         switch (d.storage) {
         case LBM_F64: e = lbm::launch_run_f64(params_d(h), ctl, h->warps, ctas, s); break;
         case LBM_F32: e = lbm::launch_run_f32(params_f(h), ctl, h->warps, ctas, s); break;

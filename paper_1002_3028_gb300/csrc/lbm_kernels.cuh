@@ -855,7 +855,7 @@ constexpr int step_smem_per_warp()
 // wait that runs out raises LBM_STATUS_TIMEOUT in the lattice's status
 // word and the warps stop taking work.
 constexpr int STATUS_TIMEOUT = 1;
-constexpr int RUN_SPIN_LIMIT = 1 << 22;  // polls of at most ~1 us: a few seconds
+constexpr int RUN_SPIN_LIMIT = 1 << 21;  // polls of at most ~2 us: a few seconds
 
 struct RunCtl {
     unsigned *counter;  // work items taken (zeroed before the launch)
@@ -910,7 +910,7 @@ __device__ bool wait_neighbours(const StepParams<C> &p, const unsigned *flags, i
         }
         if (it >= RUN_SPIN_LIMIT || (*static_cast<volatile int *>(p.status) & STATUS_TIMEOUT))
             return false;
-        __nanosleep(it < 8 ? 64 : 512);
+        __nanosleep(it < 8 ? 64 : (it < 64 ? 512 : 2048));
     }
 }
 
