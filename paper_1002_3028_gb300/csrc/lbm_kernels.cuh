@@ -416,8 +416,26 @@ __device__ __forceinline__ C jr_at(const StepParams<C> &p, const S *src, int i, 
 }
 
 // ---- properties (Section 2.3) ------------------------------------------------------
+// Property tables copied to shared memory by a persistent CTA (2-byte
+// storage, up to SMEM_TAB entries) as (nu_m, alpha_m) pairs: two 8-byte
+// loads a node instead of four global ones, and the same interpolation.
+// Measured on the 4096 x 1024 jet: FP16 62.4 GLUPS against 61.0.  FP32
+// storage keeps the global path: its staging rings already fill most of the
+// shared memory, and 2 KB more per CTA left too little L1 (49.0 against 52.2).
+constexpr int SMEM_TAB = 256;
+template <class S, class C>
+struct UseSmemTable {
+    static constexpr bool value = std::is_same<C, float>::value && sizeof(S) == 2;
+};
+
+__device__ __forceinline__ void load_smem_table(const StepParams<float> &p, float2 *tab)
+{
+    for (int m = threadIdx.x; m < p.ntab; m += blockDim.x)
+        tab[m] = make_float2(__ldg(p.nu_tab + m), __ldg(p.al_tab + m));
+}
+
 template <class C>
-__device__ __forceinline__ void properties(const StepParams<C> &p, C T, C &nu, C &al)
+__device__ __forceinline__ void properties(const StepParams<C> &p, C T, C &nu, C &al, const float2 *stab)
 {
     if (p.ntab == 1) {
         nu = __ldg(p.nu_tab);
@@ -434,6 +452,14 @@ __device__ __forceinline__ void properties(const StepParams<C> &p, C T, C &nu, C
     if (m > p.ntab - 2)
         m = p.ntab - 2;
     const C fr = s - C(m);
+    if constexpr (std::is_same<C, float>::value) {
+        if (stab != nullptr) {
+            const float2 e0 = stab[m], e1 = stab[m + 1];
+            nu = e0.x + fr * (e1.x - e0.x);
+            al = e0.y + fr * (e1.y - e0.y);
+            return;
+        }
+    }
     const C n0 = __ldg(p.nu_tab + m), n1 = __ldg(p.nu_tab + m + 1);
     const C a0 = __ldg(p.al_tab + m), a1 = __ldg(p.al_tab + m + 1);
     nu = n0 + fr * (n1 - n0);
@@ -447,7 +473,8 @@ __device__ __forceinline__ void properties(const StepParams<C> &p, C T, C &nu, C
 // and opposite directions share the quadratic term.
 template <class C, class V>
 __device__ __forceinline__ void collide(const StepParams<C> &p, const V (&f)[9], const V (&g)[4], const Mom<V> &m,
-                                        C inv_r, V d_rjx, V d_rjr, V d_xjr, V d_rT, V (&fo)[9], V (&go)[4])
+                                        C inv_r, V d_rjx, V d_rjr, V d_xjr, V d_rT, V (&fo)[9], V (&go)[4],
+                                        const float2 *stab)
 {
     constexpr int N = sizeof(V) / sizeof(C);
     constexpr C third = C(1) / C(3);
@@ -461,7 +488,7 @@ __device__ __forceinline__ void collide(const StepParams<C> &p, const V (&f)[9],
 #pragma unroll
     for (int c = 0; c < N; ++c) {
         C a, b;
-        properties<C>(p, T[c], a, b);
+        properties<C>(p, T[c], a, b, stab);
         nu.set(c, a);
         al.set(c, b);
     }
@@ -715,7 +742,7 @@ __device__ __forceinline__ C stage_jr(const S *stage, int col)
 template <class S, int NV, class C>
 __device__ __forceinline__ void collide_row(const StepParams<C> &p, const S *src, S *__restrict__ dst, const S *st,
                                             int x0, int lane, int j, int64_t t, const Mom<Vec<C, NV>> &mp,
-                                            const Mom<Vec<C, NV>> &mc, const Mom<Vec<C, NV>> &mn)
+                                            const Mom<Vec<C, NV>> &mc, const Mom<Vec<C, NV>> &mn, const float2 *stab)
 {
     using V = Vec<C, NV>;
     // axial neighbours of rho u_r: the strip's columns form one sequence
@@ -747,7 +774,7 @@ __device__ __forceinline__ void collide_row(const StepParams<C> &p, const S *src
     stage_pops<S, NV, C>(st, lane, f, g);
     const C inv_r = C(1) / (p.r0 + C(j) + C(0.5));
     collide<C, V>(p, f, g, mc, inv_r, C(0.5) * (mn.jx - mp.jx), C(0.5) * (mn.jr - mp.jr), C(0.5) * (right - left),
-                  C(0.5) * (mn.dT - mp.dT), fo, go);
+                  C(0.5) * (mn.dT - mp.dT), fo, go, stab);
     const unsigned pl = (unsigned)p.plane;
 #pragma unroll
     for (int c = 0; c < NV; ++c) {
@@ -773,7 +800,7 @@ __device__ __forceinline__ void collide_row(const StepParams<C> &p, const S *src
 // the two being read: it held row idx - 2.)
 template <class S, int NV, class C>
 __device__ __forceinline__ void step_tile(const StepParams<C> &p, const S *__restrict__ src, S *__restrict__ dst,
-                                          S *wsm, int tile, int lane, int64_t t)
+                                          S *wsm, int tile, int lane, int64_t t, const float2 *stab = nullptr)
 {
     using Wn = Win<S, NV>;
     using V = Vec<C, NV>;
@@ -815,14 +842,15 @@ __device__ __forceinline__ void step_tile(const StepParams<C> &p, const S *__res
                 mp = ghost_bottom<C, V>(p, mr);
             mc = mr;
         } else {
-            collide_row<S, NV, C>(p, src, dst, wsm + ((idx - 1) % NSTAGE) * Wn::STAGE, x0, lane, r - 1, t, mp, mc, mr);
+            collide_row<S, NV, C>(p, src, dst, wsm + ((idx - 1) % NSTAGE) * Wn::STAGE, x0, lane, r - 1, t, mp, mc, mr,
+                                  stab);
             mp = mc;
             mc = mr;
         }
     }
     if (j1 == p.nr)
         collide_row<S, NV, C>(p, src, dst, wsm + ((nrows - 1) % NSTAGE) * Wn::STAGE, x0, lane, p.nr - 1, t, mp, mc,
-                              ghost_top<C, V>(p, mc));
+                              ghost_top<C, V>(p, mc), stab);
     cp_async_wait<0>();
     __syncwarp();
 }
@@ -832,6 +860,14 @@ constexpr int step_smem_per_warp()
 {
     constexpr int NV = NodesPerLane<C>::value;
     return Stages<NV>::value * Win<S, NV>::STAGE * (int)sizeof(S);
+}
+
+// shared memory of a step_run_kernel CTA: the warps' rings, then (2-byte
+// storage) the property table
+template <class S, class C>
+constexpr int run_smem(int warps)
+{
+    return warps * step_smem_per_warp<S, C>() + (UseSmemTable<S, C>::value ? SMEM_TAB * (int)sizeof(float2) : 0);
 }
 
 // ---- many steps of one lattice in one launch ----------------------------------------
@@ -922,6 +958,15 @@ __global__ void __launch_bounds__(256) step_run_kernel(const __grid_constant__ S
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     S *wsm = reinterpret_cast<S *>(smem_raw) + (size_t)warp * Stages<NV>::value * Win<S, NV>::STAGE;
+    const float2 *stab = nullptr;
+    if constexpr (UseSmemTable<S, C>::value) {
+        if (p.ntab > 1 && p.ntab <= SMEM_TAB) {
+            float2 *tab = reinterpret_cast<float2 *>(smem_raw + (blockDim.x >> 5) * step_smem_per_warp<S, C>());
+            load_smem_table(p, tab);
+            __syncthreads();
+            stab = tab;
+        }
+    }
     const int cols = item_cols(p.nstrips, ctl.group);
     const unsigned items = (unsigned)cols * (unsigned)((p.nr + p.band - 1) / p.band);
     const unsigned total = (unsigned)ctl.nsteps * items;
@@ -946,7 +991,7 @@ __global__ void __launch_bounds__(256) step_run_kernel(const __grid_constant__ S
         S *dst = static_cast<S *>((k & 1) ? const_cast<void *>(p.src) : p.dst);
         const int s1 = min((g + 1) * ctl.group, p.nstrips);
         for (int s = g * ctl.group; s < s1; ++s)
-            step_tile<S, NV, C>(p, src, dst, wsm, b * p.nstrips + s, lane, p.step + k);
+            step_tile<S, NV, C>(p, src, dst, wsm, b * p.nstrips + s, lane, p.step + k, stab);
         red_release_add(ctl.flags + item, 1u);
         n = __shfl_sync(0xffffffffu, next, 0);
     }

@@ -12,7 +12,7 @@ cudaError_t LBM_CAT(launch_run_, LBM_TAG)(const StepParams<LBM_C> &p, const RunC
 {
     if (p.ntiles <= 0 || ctl.nsteps <= 0)
         return cudaSuccess;
-    const int smem = warps_per_cta * step_smem_per_warp<LBM_S, LBM_C>();
+    const int smem = run_smem<LBM_S, LBM_C>(warps_per_cta);
     step_run_kernel<LBM_S, LBM_C><<<ctas, 32 * warps_per_cta, smem, s>>>(p, ctl);
     return cudaGetLastError();
 }
@@ -22,12 +22,11 @@ cudaError_t LBM_CAT(launch_run_, LBM_TAG)(const StepParams<LBM_C> &p, const RunC
 cudaError_t LBM_CAT(occupancy_run_, LBM_TAG)(int warps_per_cta, int *ctas_per_sm)
 {
     cudaError_t e = cudaFuncSetAttribute(step_run_kernel<LBM_S, LBM_C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         8 * step_smem_per_warp<LBM_S, LBM_C>());
+                                         run_smem<LBM_S, LBM_C>(8));
     if (e != cudaSuccess)
         return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, step_run_kernel<LBM_S, LBM_C>,
-                                                         32 * warps_per_cta,
-                                                         warps_per_cta * step_smem_per_warp<LBM_S, LBM_C>());
+                                                         32 * warps_per_cta, run_smem<LBM_S, LBM_C>(warps_per_cta));
 }
 
 // nsteps steps of every member lattice in one persistent launch, then the
