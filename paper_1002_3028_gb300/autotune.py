@@ -18,8 +18,14 @@ from typing import Iterable, List, Optional, Sequence, Tuple
 from . import build as _build
 
 CACHE = os.path.join(_build.BUILD, "autotune.json")
-DEFAULT_CANDIDATES: Tuple[Tuple[int, int], ...] = (
-    (4, 1), (4, 2), (4, 4), (6, 2), (8, 1), (8, 2), (8, 4), (12, 2), (16, 2), (16, 4),
+# (band rows, warps per CTA).  One lattice: short bands keep many tiles between dependent
+# steps of the persistent launch; one-warp CTAs measured fastest.  A batch spreads each
+# step over many lattices and profits from longer bands.
+LATTICE_CANDIDATES: Tuple[Tuple[int, int], ...] = (
+    (1, 1), (2, 1), (3, 1), (4, 1), (5, 1), (6, 1), (7, 1), (8, 1), (6, 2),
+)
+BATCH_CANDIDATES: Tuple[Tuple[int, int], ...] = (
+    (4, 1), (6, 1), (8, 1), (12, 1), (16, 1), (16, 2),
 )
 _lock = threading.Lock()
 
@@ -92,7 +98,7 @@ def tune(target, candidates: Optional[Sequence[Tuple[int, int]]] = None, steps: 
     else:
         run = target.step
     results: List[Tuple[float, int, int]] = []
-    for band, warps in (candidates or DEFAULT_CANDIDATES):
+    for band, warps in (candidates or (BATCH_CANDIDATES if is_batch else LATTICE_CANDIDATES)):
         target.set_launch(band, warps)
         results.append((_time(run, steps, warmup), band, warps))
     results.sort()
