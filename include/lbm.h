@@ -214,6 +214,18 @@ LBM_API int lbm_diagnostics_noalloc(lbm_lattice *h, lbm_diag *out, lbm_stream st
 LBM_API int lbm_check(lbm_lattice *h, int32_t *flags);
 
 /*
+ * Self-test of the bounded waits of the persistent step launch (no
+ * counterpart in the paper).  Runs one launch on the default stream in
+ * which every work item waits for neighbours of a step that never runs,
+ * with a wait limit of a few tens of microseconds: each wait gives up,
+ * raises LBM_STATUS_TIMEOUT and its warp stops; nothing is computed or
+ * written, and the lattice's state and step count are unchanged.  Writes
+ * the status read back (LBM_STATUS_TIMEOUT when the waits behaved) to
+ * *flags and clears it.  Synchronises the device.  Not for batch members.
+ */
+LBM_API int lbm_selftest_wait_timeout(lbm_lattice *h, int32_t *flags);
+
+/*
  * Macroscopic fields at the current time: the Eq. 2 moments rho, u_x, u_r,
  * T of the populations streamed from the stored state.  dev_out is caller
  * device memory of 4 * nr * nx values of type out_type (LBM_F64 or LBM_F32),

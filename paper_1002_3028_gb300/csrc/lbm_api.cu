@@ -458,6 +458,8 @@ cudaError_t batch_launch(lbm_batch *b, int nsteps, cudaStream_t s)
     ctl.nsteps = nsteps;
     ctl.radius = b->band_eff >= 2 ? 1 : 2;
     ctl.wrap = 0;  // read from each lattice's parameters
+    ctl.spin_limit = lbm::RUN_SPIN_LIMIT;
+    ctl.group = 1;
     const int ctas = (int)std::min<int64_t>(b->ctas_max, ((int64_t)b->ntiles + b->warps - 1) / b->warps);
     switch (b->storage) {
     case LBM_F64:
@@ -738,6 +740,7 @@ int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
     ctl.flags = sync + 1;
     ctl.radius = h->band_eff >= 2 ? 1 : 2;
     ctl.wrap = d.bc_in == LBM_IN_PERIODIC ? 1 : 0;
+    ctl.spin_limit = lbm::RUN_SPIN_LIMIT;
     for (int64_t done = 0; done < nsteps;) {
         const int m = (int)std::min<int64_t>(per_launch, nsteps - done);
         cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)4 * (size_t)(1 + items), s);
@@ -759,6 +762,47 @@ int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
         done += m;
     }
     return LBM_OK;
+}
+
+int lbm_selftest_wait_timeout(lbm_lattice *h, int32_t *flags)
+{
+    if (!valid(h) || !flags)
+        return fail(LBM_ERR_INVALID_ARG, "bad handle or NULL output");
+    if (h->batch)
+        return fail(LBM_ERR_INVALID_ARG, "the lattice belongs to a batch");
+    cudaStream_t s = nullptr;
+    int rc = lbm_check(h, flags);  // start from a clear status
+    if (rc)
+        return rc;
+    const lbm_desc &d = h->d;
+    lbm::RunCtl ctl;
+    ctl.group = item_group(h);
+    const int nstrips = (d.nx + strip_cols(d.storage) - 1) / strip_cols(d.storage);
+    const unsigned items = (unsigned)lbm::item_cols(nstrips, ctl.group) * (unsigned)((d.nr + h->band_eff - 1) / h->band_eff);
+    unsigned *sync = h->at<unsigned>(h->L.off_sync);
+    ctl.counter = sync;
+    ctl.flags = sync + 1;
+    ctl.radius = h->band_eff >= 2 ? 1 : 2;
+    ctl.wrap = d.bc_in == LBM_IN_PERIODIC ? 1 : 0;
+    ctl.spin_limit = 64;  // a few tens of microseconds
+    ctl.nsteps = 2;
+    // every counter at zero and the work counter past sub-step 0: each item
+    // taken belongs to sub-step 1 and waits for a sub-step that never runs
+    cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)4 * (size_t)(1 + items), s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sync, &items, sizeof(unsigned), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        const int ctas = (int)std::min<int64_t>(h->ctas_max, ((int64_t)items + h->warps - 1) / h->warps);
+        switch (d.storage) {
+        case LBM_F64: e = lbm::launch_run_f64(params_d(h), ctl, h->warps, ctas, s); break;
+        case LBM_F32: e = lbm::launch_run_f32(params_f(h), ctl, h->warps, ctas, s); break;
+        case LBM_F16: e = lbm::launch_run_f16(params_f(h), ctl, h->warps, ctas, s); break;
+        default: e = lbm::launch_run_bf16(params_f(h), ctl, h->warps, ctas, s); break;
+        }
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(e, "self-test launch");
+    return lbm_check(h, flags);  // synchronises, reads and clears the status
 }
 
 int lbm_set_item_group(lbm_lattice *h, int32_t group)

@@ -900,6 +900,7 @@ struct RunCtl {
     int radius;         // neighbour bands an item depends on
     int wrap;           // strips wrap around (periodic axial ends; a batch reads each lattice's ends)
     int group;          // G: warp tiles (adjacent strips of one band) per work item
+    int spin_limit;     // polls before a wait gives up (RUN_SPIN_LIMIT; smaller in the self-test)
 };
 
 // work items per band of a lattice with nstrips strips
@@ -923,7 +924,7 @@ __device__ __forceinline__ void red_release_add(unsigned *a, unsigned v)
 // warp's wait ran out (the status word is read only while waiting).
 template <class C>
 __device__ bool wait_neighbours(const StepParams<C> &p, const unsigned *flags, int cols, int radius, bool wrap, int b,
-                                int g, int k)
+                                int g, int k, int spin_limit)
 {
     // lane l < 3 (2 radius + 1) watches neighbour (band b + l / 3 - radius, column g + l % 3 - 1)
     const int nbands = (p.nr + p.band - 1) / p.band;
@@ -944,7 +945,7 @@ __device__ bool wait_neighbours(const StepParams<C> &p, const unsigned *flags, i
             __syncwarp();  // orders memory among the lanes: every lane now sees what its watcher acquired
             return true;
         }
-        if (it >= RUN_SPIN_LIMIT || (*static_cast<volatile int *>(p.status) & STATUS_TIMEOUT))
+        if (it >= spin_limit || (*static_cast<volatile int *>(p.status) & STATUS_TIMEOUT))
             return false;
         __nanosleep(it < 8 ? 64 : (it < 64 ? 512 : 2048));
     }
@@ -982,7 +983,7 @@ __global__ void __launch_bounds__(256) step_run_kernel(const __grid_constant__ S
         const int k = (int)(n / items);
         const int item = (int)(n - (unsigned)k * items);
         const int b = item / cols, g = item - b * cols;
-        if (k > 0 && !wait_neighbours<C>(p, ctl.flags, cols, ctl.radius, ctl.wrap != 0, b, g, k)) {
+        if (k > 0 && !wait_neighbours<C>(p, ctl.flags, cols, ctl.radius, ctl.wrap != 0, b, g, k, ctl.spin_limit)) {
             if (lane == 0)
                 atomicOr(p.status, STATUS_TIMEOUT);
             break;  // whole warp
@@ -1045,7 +1046,7 @@ __global__ void __launch_bounds__(256) batch_run_kernel(const TileRef *__restric
         __syncwarp();
         const StepParams<C> &p = *pw;
         if (k > 0 && !wait_neighbours<C>(p, ctl.flags + (idx - t.tile), p.nstrips, ctl.radius, p.bc_in == IN_PERIODIC,
-                                         t.tile / p.nstrips, t.tile % p.nstrips, k)) {
+                                         t.tile / p.nstrips, t.tile % p.nstrips, k, ctl.spin_limit)) {
             if (lane == 0)
                 atomicOr(p.status, STATUS_TIMEOUT);
             break;  // whole warp

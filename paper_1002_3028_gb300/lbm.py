@@ -109,6 +109,7 @@ def lib(build: bool = True):
             L.lbm_set_launch.argtypes = [vp, i32, i32]
             L.lbm_get_launch.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
             L.lbm_set_item_group.argtypes = [vp, i32]
+            L.lbm_selftest_wait_timeout.argtypes = [vp, C.POINTER(i32)]
             L.lbm_get_item_group.restype = i32
             L.lbm_get_item_group.argtypes = [vp]
             L.lbm_check.argtypes = [vp, C.POINTER(i32)]
@@ -219,6 +220,12 @@ class Lattice:
     def set_launch(self, band_rows: int = 0, warps_per_cta: int = 0):
         """band_rows 0 = automatic (one wave of resident warps); warps 0 = unchanged."""
         _check(self._L.lbm_set_launch(self._h, band_rows, warps_per_cta), "lbm_set_launch")
+
+    def selftest_wait_timeout(self) -> int:
+        """Run a launch whose waits can never be met; returns the device status it raised."""
+        v = C.c_int32()
+        _check(self._L.lbm_selftest_wait_timeout(self._h, C.byref(v)), "lbm_selftest_wait_timeout")
+        return v.value
 
     def set_item_group(self, group: int = 0):
         """Warp tiles per work item of the persistent step launch (0 = automatic)."""

@@ -259,6 +259,27 @@ def test_many_steps_in_one_launch_equal_single_steps(lbm, orc, storage, bounds, 
     assert one.check() == 0 and many.check() == 0
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16", "f64"])
+def test_bounded_waits_time_out_and_leave_the_lattice_usable(lbm, orc, storage):
+    """A launch whose dependency waits can never be met ends by itself with
+    LBM_STATUS_TIMEOUT; the state is untouched and the next steps are exact."""
+    w = workload(150, 45)
+    a = lbm.Lattice.from_workload(w, storage)
+    b = lbm.Lattice.from_workload(w, storage)
+    f0, g0 = I.random_state(150, 45, orc.feq(1.0, 0.02, 0.0), orc.geq(1.2, 0.02, 0.0), 0.05, 31)
+    for lat in (a, b):
+        lat.set_state(f0, g0, 0)
+        lat.step(3)
+    before, _ = a.save()
+    assert a.selftest_wait_timeout() == 1  # LBM_STATUS_TIMEOUT
+    after, step = a.save()
+    assert step == 3 and torch.equal(before, after)
+    assert a.check() == 0  # the self-test cleared what it raised
+    a.step(5)
+    b.step(5)
+    assert torch.equal(a.save()[0], b.save()[0])
+
+
 def test_rest_state_is_exactly_steady(lbm):
     cfg = I.LatticeConfig(nx=100, nr=30, bc_top="wall", T_top=1.0)
     lat = lbm.Lattice(cfg, "f32")
