@@ -297,6 +297,8 @@ def run_gpu(args):
         autotune.tune(target)
     elif args.band or args.warps:
         target.set_launch(max(args.band, 0), args.warps)
+    if args.group > 0 and len(lats) == 1:
+        target.set_item_group(args.group)
 
     def barrier():
         replicas.barrier()
@@ -449,6 +451,8 @@ def main(argv=None):
     ap.add_argument("--storage", default="f32", choices=sorted(BYTES_PER_VALUE))
     ap.add_argument("--band", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--group", type=int, default=0,
+                    help="one lattice: warp tiles per work item of the persistent launch (0 = automatic)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="tune the launch shape before timing")
