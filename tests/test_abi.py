@@ -57,7 +57,7 @@ def test_required_bytes_counts_two_buffers():
 
 
 @pytest.mark.parametrize("bad", [
-    dict(nx=0), dict(nr=0), dict(bc_in="periodic"), dict(r0=1.0),
+    dict(nx=0), dict(nr=0), dict(bc_in="periodic"), dict(r0=1.0), dict(nx=40000, nr=5000),
 ])
 def test_invalid_descriptions_are_rejected(bad):
     cfg = I.LatticeConfig(nx=10, nr=10)

@@ -134,3 +134,34 @@ def test_batch_member_matches_oracle(lbm, orc):
         assert np.max(np.abs(fg[q].cpu().numpy() - fo[q])) <= 1e-12 * np.max(np.abs(fo[q]))
     for q in range(4):
         assert np.max(np.abs(gg[q].cpu().numpy() - go[q])) <= 1e-12 * np.max(np.abs(go[q]))
+
+
+@pytest.mark.parametrize("storage,bar", [("f32", 2e-5), ("f16", 2e-3)])
+def test_full_ensemble_batch_matches_oracle(lbm, orc, storage, bar):
+    """The benchmark's ensemble (256 ragged jets, 23.2 M nodes) in its own launch
+    configuration: two batched steps from random states on sampled members, against the
+    oracle (per-step bars of the parity tests, times two steps)."""
+    ws = I.ensemble_workloads(256, seed=7)
+    lats = [lbm.Lattice.from_workload(w, storage) for w in ws]
+    b = lbm.Batch(storage)
+    for x in lats:
+        b.add(x)
+    picks = [0, 77, 154, 255]
+    orcs = {}
+    for k in picks:
+        w = ws[k]
+        f0, g0 = I.random_state(w.cfg.nx, w.cfg.nr, orc.feq(1.0, 0.02, 0.0), orc.geq(1.5, 0.0, 0.0), 0.03, 100 + k)
+        o = orc.Oracle.from_workload(w, NTHREADS)
+        o.set_state(f0, g0, 9)
+        lats[k].set_state(f0, g0, 9)
+        orcs[k] = o
+    b.step(2, graph=False)
+    for k, o in orcs.items():
+        o.step(2)
+        fg, gg = lats[k].get_state()
+        fo, go = o.get_state()
+        for q in range(9):
+            assert np.max(np.abs(fg[q].cpu().numpy() - fo[q])) <= bar * np.max(np.abs(fo[q])), (k, q)
+        for q in range(4):
+            assert np.max(np.abs(gg[q].cpu().numpy() - go[q])) <= bar * np.max(np.abs(go[q])), (k, q)
+    assert max(x.check() for x in lats) == 0
