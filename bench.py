@@ -254,6 +254,33 @@ def run_reference(args):
     return 0
 
 
+def error_vs_f64(works, storage: str, device, steps: int = 1000, sample: int = 4):
+    """Field errors of the measured storage type against the FP64 GPU path (which the parity
+    tests hold to the oracle within 1e-12 per step): up to `sample` lattices of the workload
+    run `steps` steps from the same start in both, and the largest relative errors of rho,
+    u (against the maximum speed) and T are reported."""
+    if storage == "f64":
+        return {"vs": "FP64 oracle (parity tests)", "bound_per_step": 1e-12}
+    from paper_1002_3028_gb300 import lbm
+
+    picks = list(range(0, len(works), max(1, len(works) // sample)))[:sample]
+    worst = {"rho": 0.0, "u": 0.0, "T": 0.0}
+    for k in picks:
+        a = lbm.Lattice.from_workload(works[k], storage, device=device)
+        b = lbm.Lattice.from_workload(works[k], "f64", device=device)
+        a.step(steps)
+        b.step(steps)
+        Fa, Fb = a.fields(), b.fields()
+        speed = float(Fb[1:3].abs().max())
+        worst["rho"] = max(worst["rho"], float((Fa[0] - Fb[0]).abs().max() / Fb[0].abs().max()))
+        worst["u"] = max(worst["u"], float((Fa[1:3] - Fb[1:3]).abs().max()) / max(speed, 1e-30))
+        worst["T"] = max(worst["T"], float((Fa[3] - Fb[3]).abs().max() / Fb[3].abs().max()))
+        a.close()
+        b.close()
+    return {"vs": "FP64 GPU path (held to the oracle within 1e-12 per step by the parity tests)",
+            "steps": steps, "lattices": len(picks), **worst}
+
+
 def step_launches(lats, storage: str, launch, steps: int) -> int:
     """Kernels launched by `steps` steps.  One lattice runs its steps in persistent launches
     of up to 2^31 / (2 x warp tiles) steps each.  A batch replays a captured launch of 64
@@ -360,6 +387,7 @@ def run_gpu(args):
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
            "note": "initial states uploaded, K steps, fields downloaded; copies amortised over K"}
 
+    errors = error_vs_f64(works, args.storage, device)
     if rank != 0:
         replicas.finish()
         return 0
@@ -384,6 +412,7 @@ def run_gpu(args):
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                      "per": "step (the timed steps run in persistent launches of many steps)"},
         "cpu_baseline": cpu,
+        "error": errors,
         "e2e": e2e,
         "gpu_launches": step_launches(lats, args.storage, launch, args.steps),
         "clocks": clk.summary(),
@@ -427,11 +456,11 @@ def run_serving(args):
     b, p_ = batched.summary(), plain.summary()
     line = {
         "metric": METRIC, "value": b["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": None, "warmup": 0,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16 storage, f32 math",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": f"serving: {len(reqs)} Poisson requests at {args.rate}/s, jets drawn like the "
-                               f"ensemble, steps U{{1000..20000}}, seed 11", "budget_gb": args.budget_gb,
-                   "chunk_steps": args.chunk},
+                               f"ensemble, steps U{{1000..20000}}, seed 11", "storage": "f16 (batched), f32 (plain)",
+                   "budget_gb": args.budget_gb, "chunk_steps": args.chunk},
         "serving": {"batched_f16": b, "plain_f32_one_at_a_time": p_,
                     "mlups_ratio_batched_over_plain": b["mlups"] / p_["mlups"],
                     "f16_error_vs_f64_sample": errs},
