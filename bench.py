@@ -69,8 +69,12 @@ def measured_peaks():
 
 
 def kernel_hash() -> str:
-    with open(KERNEL_SRC, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    """First 16 hex digits of the SHA-256 of the kernel source's code: every line cut at `//`,
+    trailing blanks and empty lines dropped, so that comment edits keep the hash."""
+    with open(KERNEL_SRC) as fh:
+        lines = (ln.split("//", 1)[0].rstrip() for ln in fh.read().splitlines())
+    code = "\n".join(ln for ln in lines if ln)
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
 def ncu_traffic(storage: str, workload: str):
@@ -81,7 +85,7 @@ def ncu_traffic(storage: str, workload: str):
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    h = re.search(r"kernel_code_sha256_16:\s*([0-9a-f]+)", text)
     b = re.search(r"dram_bytes_per_step_full_size:\s*([0-9.eE+]+)", text)
     if not h or not b or h.group(1) != kernel_hash():
         return None

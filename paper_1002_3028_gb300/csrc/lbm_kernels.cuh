@@ -26,11 +26,16 @@
 // x0 + 32 + lane, computed together with the paired FP32x2 instructions;
 // NV = 1 in FP64) and marches up a band of rows.  The populations each row
 // pulls are staged in the warp's shared-memory ring by asynchronous copies
-// issued two rows ahead; from a landed row the warp forms the Eq. 2 moments
-// and collides the row below, whose radial neighbours' moments (same time
-// level) it already holds.  The axial neighbours' rho u_r come from the
-// adjacent columns by warp shuffle and, for the two columns beside the
-// strip, from the staged window's halo.
+// issued one row ahead (two in FP64); from a landed row the warp forms the
+// Eq. 2 moments and collides the row below, whose radial neighbours' moments
+// (same time level) it already holds.  The axial neighbours' rho u_r come
+// from the adjacent columns by warp shuffle and, for the two columns beside
+// the strip, from the staged window's halo.
+//
+// Launches.  All steps of one lbm_step call run in one persistent launch
+// (step_run_kernel; batches: batch_run_kernel): warps take warp tiles in
+// step-major order, and a tile of step t + 1 starts once the tiles around it
+// have finished step t (see "many steps of one lattice in one launch").
 #pragma once
 
 #include <cuda_bf16.h>
