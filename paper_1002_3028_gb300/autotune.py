@@ -75,12 +75,14 @@ def _time(step_fn, steps: int, warmup: int) -> float:
     return e0.elapsed_time(e1) / steps
 
 
-def tune(target, candidates: Optional[Sequence[Tuple[int, int]]] = None, steps: int = 50, warmup: int = 5,
+def tune(target, candidates: Optional[Sequence[Tuple[int, int]]] = None, steps: int = 400, warmup: int = 20,
          use_cache: bool = True) -> Tuple[int, int]:
     """Pick and set the fastest (band rows, warps per CTA) for a Lattice or Batch.
 
     Returns the chosen shape.  With use_cache, a shape tuned earlier for the
-    same GPU, storage and lattice shapes is applied without timing.
+    same GPU, storage and lattice shapes is applied without timing.  Each
+    candidate runs `steps` steps in one persistent launch (enough that the
+    launch's ramp and tail do not decide the ranking), twice.
     """
     from .lbm import Batch
 
@@ -97,11 +99,18 @@ def tune(target, candidates: Optional[Sequence[Tuple[int, int]]] = None, steps: 
             target.step(n, graph=False)
     else:
         run = target.step
-    results: List[Tuple[float, int, int]] = []
-    for band, warps in (candidates or (BATCH_CANDIDATES if is_batch else LATTICE_CANDIDATES)):
-        target.set_launch(band, warps)
-        results.append((_time(run, steps, warmup), band, warps))
-    results.sort()
+    cands = list(candidates or (BATCH_CANDIDATES if is_batch else LATTICE_CANDIDATES))
+    # bring the GPU to its working clocks first, then time every candidate twice, in
+    # opposite orders, and keep each one's best: a fixed order would favour whichever
+    # candidate runs last on a warming GPU
+    run(max(warmup, steps))
+    best = {}
+    for order in (cands, cands[::-1]):
+        for band, warps in order:
+            target.set_launch(band, warps)
+            ms = _time(run, steps, warmup)
+            best[(band, warps)] = min(ms, best.get((band, warps), ms))
+    results: List[Tuple[float, int, int]] = sorted((ms, b, w) for (b, w), ms in best.items())
     ms, band, warps = results[0]
     target.set_launch(band, warps)
     _store(key, {"band": band, "warps": warps, "ms_per_step": ms,
