@@ -198,19 +198,23 @@ def test_single_jet_1024x256_per_step(lbm, orc, storage, tol):
         assert state_rel(g.get_state(), o.get_state()) < tol
 
 
-def test_full_size_4096x1024_one_step(lbm, orc):
-    """The 4096 x 1024 jet (the throughput workload), FP32, one step from a perturbed rest state."""
+@pytest.mark.parametrize("storage,bar", [("f32", 1e-5), ("f16", 1e-3), ("bf16", 3e-3)])
+def test_full_size_4096x1024(lbm, orc, storage, bar):
+    """The 4096 x 1024 jet (the throughput workload) in the benchmark's launch configuration:
+    three steps in one persistent launch from a perturbed state, against the oracle (the
+    per-step bar of the storage type, times three)."""
     w = I.jet_workload(nx=4096, nr=1024)
     o = orc.Oracle.from_workload(w, NTHREADS)
-    g = lbm.Lattice.from_workload(w, "f32")
+    g = lbm.Lattice.from_workload(w, storage)
     f0, g0 = I.random_state(4096, 1024, orc.feq(1.0, 0.03, 0.0), orc.geq(2.0, 0.03, 0.0), 0.01, 4)
     o.set_state(f0, g0, 17)
     g.set_state(f0, g0, 17)
     del f0, g0
-    o.step(1)
-    g.step(1)
+    o.step(3)
+    g.step(3)
     errs = fields_rel(g.fields(), o.fields())
-    assert max(errs) < 1e-5, errs
+    assert max(errs) < 3 * bar, errs
+    assert g.check() == 0
 
 
 @pytest.mark.parametrize("band,warps", [(1, 1), (3, 8), (16, 4), (64, 2), (1000, 4)])
