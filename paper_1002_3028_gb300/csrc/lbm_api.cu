@@ -1,5 +1,6 @@
 // C ABI of liblbm (declared in include/lbm.h): lattice handles, device
-// memory layout, table uploads and the per-step launch loop.
+// memory layout, table uploads, the persistent multi-step launches of one
+// lattice and of batches, state I/O, checkpoints and diagnostics.
 #include <cuda_runtime.h>
 
 #include <algorithm>
