@@ -754,6 +754,9 @@ __device__ __forceinline__ void collide_row(const StepParams<C> &p, const S *src
     // c = lane + 32 v; its ends read the staged halo, the lattice ends the
     // boundary's ghost moments
     V left, right;
+    // rho u_r beside the strip, computed by every lane for its half's side
+    // (lanes 0..15 the left, 16..31 the right) in one warp-uniform pass
+    const C beside = stage_jr<S, NV, C>(st, lane < 16 ? -1 : 32 * NV);
 #pragma unroll
     for (int c = 0; c < NV; ++c) {
         const C up = __shfl_up_sync(0xffffffffu, mc.jr[c], 1);
@@ -762,9 +765,9 @@ __device__ __forceinline__ void collide_row(const StepParams<C> &p, const S *src
         const C next_first = __shfl_sync(0xffffffffu, mc.jr[(c + 1) % NV], 0);
         C l = up, r = dn;
         if (lane == 0)
-            l = (c == 0) ? stage_jr<S, NV, C>(st, -1) : prev_last;
+            l = (c == 0) ? beside : prev_last;
         if (lane == 31)
-            r = (c == NV - 1) ? stage_jr<S, NV, C>(st, 32 * NV) : next_first;
+            r = (c == NV - 1) ? beside : next_first;
         const int i = x0 + lane + 32 * c;
         if (i == 0)
             l = jr_beyond_inlet<S, C>(p, src, j);
