@@ -14,7 +14,8 @@
  *     axisymmetric model, the paper's ref. [4]),
  *   - the inlet profiles of Eq. 7 (Section 2.4) and axis, wall, open and
  *     outflow boundaries.
- * Every step is one fused pull-stream + collide kernel on the GPU.
+ * Every step is one pass of a fused pull-stream + collide kernel on the GPU;
+ * the steps of one call run in one persistent launch.
  *
  * Conventions (all lattice units, dx = dt = 1):
  *   x is axial (index i, 0 <= i < nx); r is radial (index j, 0 <= j < nr);
