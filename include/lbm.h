@@ -74,6 +74,21 @@ typedef enum { LBM_OUT_OUTFLOW = 0, LBM_OUT_WALL = 1, LBM_OUT_PERIODIC = 2 } lbm
 typedef enum { LBM_TOP_WALL = 0, LBM_TOP_OPEN = 1 } lbm_bc_top;
 typedef enum { LBM_BOTTOM_AXIS = 0, LBM_BOTTOM_WALL = 1 } lbm_bc_bottom;
 
+/* Memory layout of the populations (lbm_desc.pattern).
+ *   LBM_PATTERN_AB  two buffers: each step pulls from one and writes the
+ *                   other (the default).
+ *   LBM_PATTERN_AA  one buffer updated in place (the "AA" pattern of
+ *                   Bailey et al., ICPP 2009), plus 4 planes of the last
+ *                   step's moments in the arithmetic type: 13 populations
+ *                   + 4 moments per node instead of 26 populations (FP32:
+ *                   68 instead of 104 bytes per node; FP16/BF16: 42
+ *                   instead of 52; FP64: 136 instead of 208).  Each step is
+ *                   two passes in one launch (moments, then collision; the
+ *                   same-time neighbour moments of Eq. 1's sources need the
+ *                   first).  Results are bit for bit those of LBM_PATTERN_AB.
+ *                   Not for batch members. */
+typedef enum { LBM_PATTERN_AB = 0, LBM_PATTERN_AA = 1 } lbm_pattern;
+
 /*
  * Lattice description (Section 2.4: a half-plane of nx x nr nodes whose
  * inlet edge carries the profiles of Eq. 7).
@@ -109,13 +124,15 @@ typedef struct {
     double T_top, T_bottom, T_out; /* wall temperatures */
     double noise_amp;    /* amplitude of the inlet velocity noise */
     uint64_t seed;       /* seed of the inlet noise */
+    int32_t pattern;     /* lbm_pattern (0 = LBM_PATTERN_AB) */
 } lbm_desc;
 
 /* Message of the last failed call on this host thread ("" if none). */
 LBM_API const char *lbm_last_error(void);
 
-/* Bytes of device memory a lattice needs (two population buffers plus
- * tables, 256-byte aligned).  Returns LBM_ERR_INVALID_ARG for a bad desc. */
+/* Bytes of device memory a lattice needs (two population buffers, or one
+ * and the moment planes for LBM_PATTERN_AA, plus tables; 256-byte
+ * aligned).  Returns LBM_ERR_INVALID_ARG for a bad desc. */
 LBM_API int lbm_required_bytes(const lbm_desc *d, size_t *bytes);
 
 /*
@@ -154,8 +171,9 @@ LBM_API int lbm_set_properties(lbm_lattice *h, const double *nu, const double *a
 /*
  * Advance nsteps >= 0 time steps (Eq. 1).  All the steps run in one
  * persistent launch of the fused kernel (more than one only when nsteps x
- * warp tiles exceeds 2^30): a warp tile of step t + 1 starts once the tiles
- * around it have finished step t.  The result is bit for bit that of nsteps
+ * warp tiles exceeds 2^30, or for small LBM_PATTERN_AA lattices, see
+ * lbm_set_aa_lag): a warp tile of step t + 1 starts once the tiles around
+ * it have finished step t.  The result is bit for bit that of nsteps
  * one-step calls.  Asynchronous; returns LBM_ERR_CUDA if a launch fails.  A
  * wait that runs out (it cannot in a correct launch; it is bounded all the
  * same) raises LBM_STATUS_TIMEOUT (see lbm_check) and ends the launch early.
@@ -215,8 +233,8 @@ LBM_API int lbm_diagnostics_noalloc(lbm_lattice *h, lbm_diag *out, lbm_stream st
 LBM_API int lbm_check(lbm_lattice *h, int32_t *flags);
 
 /*
- * Self-test of the bounded waits of the persistent step launch (no
- * counterpart in the paper).  Runs one launch on the default stream in
+ * Self-test of the bounded waits of the persistent step launch (either
+ * pattern's; no counterpart in the paper).  Runs one launch on the default stream in
  * which every work item waits for neighbours of a step that never runs,
  * with a wait limit of a few tens of microseconds: each wait gives up,
  * raises LBM_STATUS_TIMEOUT and its warp stops; nothing is computed or
@@ -252,13 +270,14 @@ LBM_API int lbm_set_state(lbm_lattice *h, const double *dev_f, const double *dev
  *
  * lbm_checkpoint_bytes: size of a checkpoint, 13 * nr * nx values of the
  *   storage type (8, 4 or 2 bytes).
- * lbm_save: copy the stored populations, as deviations from rest
- *   (f_k - w_k rho0 and g_k - T0 / 4, in the storage type), into dev_out,
+ * lbm_save: copy the stored post-collision populations, as deviations
+ *   from rest (f_k - w_k rho0 and g_k - T0 / 4, in the storage type; the
+ *   same values and layout for both patterns), into dev_out,
  *   caller device memory of lbm_checkpoint_bytes bytes, layout
  *   [q][j][i] with q = f0..f8, g0..g3.  The step counter is read with
  *   lbm_get_step.  Asynchronous on the stream.
- * lbm_restore: the reverse, into a lattice with the same description
- *   (size and storage), and set its step counter to step (>= 0); the
+ * lbm_restore: the reverse, into a lattice of the same size and storage
+ *   (either pattern), and set its step counter to step (>= 0); the
  *   boundary ghosts are recomputed.  The next lbm_diagnostics residual has
  *   no previous state.  Returns LBM_ERR_INVALID_ARG for a NULL buffer or a
  *   negative step.
@@ -281,6 +300,16 @@ LBM_API int lbm_set_launch(lbm_lattice *h, int32_t band_rows, int32_t warps_per_
  * launch (any pointer may be NULL). */
 LBM_API int lbm_get_launch(const lbm_lattice *h, int32_t *band_rows, int32_t *warps_per_cta, int32_t *ctas);
 
+/* LBM_PATTERN_AA lattices: the lag of the collision pass behind the moments
+ * pass in lbm_step's launch, in work items (0 = automatic: one band of
+ * items plus half the warps resident at once).  It is clamped to the range
+ * in which every wait is on earlier work; lattices with fewer than about
+ * three bands of items run one step per launch instead.  Results do not
+ * depend on it.  lbm_get_aa_lag returns the lag lbm_step uses (0 for one
+ * step per launch, -1 for a bad handle or a two-buffer lattice). */
+LBM_API int lbm_set_aa_lag(lbm_lattice *h, int32_t lag);
+LBM_API int32_t lbm_get_aa_lag(const lbm_lattice *h);
+
 /* Work-item size of lbm_step's persistent launch: a warp takes `group`
  * adjacent warp tiles of one band at a time and synchronises with its
  * neighbours once per item (1..64; 0 = automatic).  Results do not depend
@@ -297,7 +326,7 @@ LBM_API int32_t lbm_get_item_group(const lbm_lattice *h);
  *                      change the membership (takes effect at the next
  *                      lbm_batch_step; a lattice belongs to one batch at a
  *                      time; lbm_step on a member is an error; lbm_destroy
- *                      removes it).  Members keep their own state, inlet,
+ *                      removes it; LBM_PATTERN_AA lattices are refused).  Members keep their own state, inlet,
  *                      tables and step counter; lbm_get_fields and friends
  *                      work on members as usual.
  *   lbm_batch_step     nsteps steps of every member on the stream; with

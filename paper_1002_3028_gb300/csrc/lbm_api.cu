@@ -63,7 +63,8 @@ struct Layout {
     int pitch;
     int64_t plane;
     size_t buf_bytes;                    // one population buffer (13 planes)
-    size_t off_buf[2];
+    size_t off_buf[2];                   // the same buffer twice for the AA pattern
+    size_t off_mom;                      // AA pattern: 4 moment planes of the arithmetic type
     size_t off_uin_d, off_tin_d, off_uin_f, off_tin_f;
     size_t off_nu_d, off_al_d, off_nu_f, off_al_f;
     size_t off_status;
@@ -87,6 +88,8 @@ int check_desc(const lbm_desc *d)
     // the step kernel addresses a population buffer with 32-bit element offsets
     if (13 * (int64_t)row_pitch(d->nx) * (d->nr + 2) >= INT32_MAX)
         return fail(LBM_ERR_INVALID_ARG, "lattice %d x %d exceeds 13 * (nr + 2) * pitch < 2^31 elements", d->nx, d->nr);
+    if (d->pattern != LBM_PATTERN_AB && d->pattern != LBM_PATTERN_AA)
+        return fail(LBM_ERR_INVALID_ARG, "unknown pattern %d", d->pattern);
     if (d->bc_in < 0 || d->bc_in > 1 || d->bc_out < 0 || d->bc_out > 2 || d->bc_top < 0 || d->bc_top > 1 ||
         d->bc_bottom < 0 || d->bc_bottom > 1)
         return fail(LBM_ERR_INVALID_ARG, "unknown boundary kind");
@@ -107,11 +110,14 @@ Layout make_layout(const lbm_desc *d)
     L.pitch = row_pitch(d->nx);
     L.plane = (int64_t)L.pitch * (d->nr + 2);  // ghost rows -1 and nr
     L.buf_bytes = align_up((size_t)13 * (size_t)L.plane * storage_bytes(d->storage));
+    const bool aa = d->pattern == LBM_PATTERN_AA;
     size_t o = 0;
     L.off_buf[0] = o;
     o += L.buf_bytes;
-    L.off_buf[1] = o;
-    o += L.buf_bytes;
+    L.off_buf[1] = aa ? L.off_buf[0] : o;
+    o += aa ? 0 : L.buf_bytes;
+    L.off_mom = o;
+    o += aa ? align_up((size_t)4 * (size_t)L.plane * (d->storage == LBM_F64 ? 8 : 4)) : 0;
     const size_t nrd = align_up((size_t)d->nr * 8), nrf = align_up((size_t)d->nr * 4);
     L.off_uin_d = o; o += nrd;
     L.off_tin_d = o; o += nrd;
@@ -123,8 +129,8 @@ Layout make_layout(const lbm_desc *d)
     L.off_nu_f = o; o += tf;
     L.off_al_f = o; o += tf;
     L.off_status = o; o += kAlign;
-    // warp tiles are at least 32 columns by one row
-    L.off_sync = o; o += align_up((size_t)4 * (1 + (size_t)((d->nx + 31) / 32) * (size_t)d->nr));
+    // warp tiles are at least 32 columns by one row; the AA pattern counts both passes
+    L.off_sync = o; o += align_up((size_t)4 * (1 + (aa ? 2 : 1) * (size_t)((d->nx + 31) / 32) * (size_t)d->nr));
     L.off_diag = o; o += align_up((size_t)(lbm::DIAG_MAX_BLOCKS + 1) * lbm::DIAG_SLOTS * sizeof(double));
     L.total = o;
     return L;
@@ -150,6 +156,9 @@ struct lbm_lattice {
     int ctas_max;          // CTAs resident on the device at once (persistent grid)
     int group;             // warp tiles per work item of lbm_step (0 = automatic)
     int device, sms;
+    bool aa;               // AA pattern: one buffer (cur stays 0), moment planes
+    int phase;             // AA pattern: representation of the stored state (lbm_aa.cuh)
+    int lag;               // AA pattern: lag of pass B in work items (0 = automatic)
 
     void *buf(int b) const { return mem + L.off_buf[b]; }
     template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(mem + off); }
@@ -216,6 +225,9 @@ lbm::StepParams<C> make_params(const lbm_lattice *h, const C *u_in, const C *T_i
     p.nu_tab = nu;
     p.al_tab = al;
     p.status = h->at<int>(h->L.off_status);
+    p.aa = h->aa ? 1 : 0;
+    p.phase = h->aa ? h->phase : 0;
+    p.mom = h->aa ? h->at<C>(h->L.off_mom) : nullptr;
     return p;
 }
 
@@ -251,10 +263,10 @@ int plan_launch(lbm_lattice *h)
     int per_sm = 0;
     cudaError_t e;
     switch (h->d.storage) {
-    case LBM_F64: e = lbm::occupancy_run_f64(h->warps, &per_sm); break;
-    case LBM_F32: e = lbm::occupancy_run_f32(h->warps, &per_sm); break;
-    case LBM_F16: e = lbm::occupancy_run_f16(h->warps, &per_sm); break;
-    default: e = lbm::occupancy_run_bf16(h->warps, &per_sm); break;
+    case LBM_F64: e = h->aa ? lbm::occupancy_aa_run_f64(h->warps, &per_sm) : lbm::occupancy_run_f64(h->warps, &per_sm); break;
+    case LBM_F32: e = h->aa ? lbm::occupancy_aa_run_f32(h->warps, &per_sm) : lbm::occupancy_run_f32(h->warps, &per_sm); break;
+    case LBM_F16: e = h->aa ? lbm::occupancy_aa_run_f16(h->warps, &per_sm) : lbm::occupancy_run_f16(h->warps, &per_sm); break;
+    default: e = h->aa ? lbm::occupancy_aa_run_bf16(h->warps, &per_sm) : lbm::occupancy_run_bf16(h->warps, &per_sm); break;
     }
     if (e != cudaSuccess)
         return cuda_fail(e, "occupancy query");
@@ -276,10 +288,60 @@ int plan_launch(lbm_lattice *h)
     return LBM_OK;
 }
 
+// Schedule of an AA-pattern launch (lbm_aa.cuh): items per step, the lag
+// L of pass B behind pass A, and steps per launch.  With D the largest
+// item-index distance between neighbour items, every wait is on an earlier
+// job when D <= L <= items - 1 - D; lattices with items < 2 D + 1 run one
+// step per launch with L = items (all of pass A first).
+struct AAPlan {
+    int64_t items, lag, per_launch;
+    bool multi;  // several steps per launch
+};
+
+AAPlan aa_plan(const lbm_lattice *h, int group)
+{
+    const lbm_desc &d = h->d;
+    const int nstrips = (d.nx + strip_cols(d.storage) - 1) / strip_cols(d.storage);
+    const int64_t cols = lbm::item_cols(nstrips, group);
+    AAPlan a;
+    a.items = cols * ((d.nr + h->band_eff - 1) / h->band_eff);
+    const int64_t D = d.bc_in == LBM_IN_PERIODIC ? 2 * cols - 1 : cols + 1;
+    a.multi = a.items >= 2 * D + 1;
+    if (a.multi) {
+        const int64_t want = h->lag > 0 ? h->lag : D + (int64_t)h->ctas_max * h->warps / 2;
+        a.lag = std::min(std::max(want, D), a.items - 1 - D);
+        // jobs 2 (steps x items + lag) stay below 2^31
+        a.per_launch = std::max<int64_t>(1, (((int64_t)1 << 30) - 1 - a.lag) / a.items);
+    } else {
+        a.lag = a.items;
+        a.per_launch = 1;
+    }
+    return a;
+}
+
+cudaError_t aa_launch(lbm_lattice *h, const lbm::RunCtl &ctl, int lag, int ctas, cudaStream_t s)
+{
+    switch (h->d.storage) {
+    case LBM_F64: return lbm::launch_aa_run_f64(params_d(h), ctl, lag, h->warps, ctas, s);
+    case LBM_F32: return lbm::launch_aa_run_f32(params_f(h), ctl, lag, h->warps, ctas, s);
+    case LBM_F16: return lbm::launch_aa_run_f16(params_f(h), ctl, lag, h->warps, ctas, s);
+    default: return lbm::launch_aa_run_bf16(params_f(h), ctl, lag, h->warps, ctas, s);
+    }
+}
+
 // recompute the boundary ghosts of the current state (after it or the inlet changed)
 int fill_ghosts(lbm_lattice *h, cudaStream_t s)
 {
     cudaError_t e;
+    if (h->aa) {
+        switch (h->d.storage) {
+        case LBM_F64: e = lbm::launch_aa_fill_f64(params_d(h), s); break;
+        case LBM_F32: e = lbm::launch_aa_fill_f32(params_f(h), s); break;
+        case LBM_F16: e = lbm::launch_aa_fill_f16(params_f(h), s); break;
+        default: e = lbm::launch_aa_fill_bf16(params_f(h), s); break;
+        }
+        return e == cudaSuccess ? LBM_OK : cuda_fail(e, "ghost fill kernel launch");
+    }
     switch (h->d.storage) {
     case LBM_F64: {
         auto p = params_d(h);
@@ -608,6 +670,9 @@ int lbm_create(const lbm_desc *d, void *dev_mem, size_t bytes, lbm_lattice **out
     h->band = 0;
     h->warps = 1;
     h->group = 0;
+    h->aa = d->pattern == LBM_PATTERN_AA;
+    h->phase = 0;
+    h->lag = 0;
     cudaGetDevice(&h->device);
     h->sms = 1;
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -732,6 +797,31 @@ int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
     const lbm_desc &d = h->d;
     lbm::RunCtl ctl;
     ctl.group = item_group(h);
+    if (h->aa) {
+        const AAPlan a = aa_plan(h, ctl.group);
+        unsigned *sync = h->at<unsigned>(h->L.off_sync);
+        ctl.counter = sync;
+        ctl.flags = sync + 1;
+        ctl.radius = 1;
+        ctl.wrap = d.bc_in == LBM_IN_PERIODIC ? 1 : 0;
+        ctl.spin_limit = lbm::RUN_SPIN_LIMIT;
+        const int ctas = (int)std::min<int64_t>(h->ctas_max, (a.items + h->warps - 1) / h->warps);
+        for (int64_t done = 0; done < nsteps;) {
+            const int m = (int)std::min<int64_t>(a.per_launch, nsteps - done);
+            cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)4 * (size_t)(1 + 2 * a.items), s);
+            if (e != cudaSuccess)
+                return cuda_fail(e, "work counter reset");
+            ctl.nsteps = m;
+            e = aa_launch(h, ctl, (int)a.lag, ctas, s);
+            if (e != cudaSuccess)
+                return cuda_fail(e, "step kernel launch");
+            h->phase ^= (m & 1);
+            h->step += m;
+            h->prev_valid = true;
+            done += m;
+        }
+        return LBM_OK;
+    }
     const int nstrips = (d.nx + strip_cols(d.storage) - 1) / strip_cols(d.storage);
     const int64_t items = (int64_t)lbm::item_cols(nstrips, ctl.group) * ((d.nr + h->band_eff - 1) / h->band_eff);
     // steps per launch: the work counter stays below 2^31
@@ -787,6 +877,21 @@ int lbm_selftest_wait_timeout(lbm_lattice *h, int32_t *flags)
     ctl.wrap = d.bc_in == LBM_IN_PERIODIC ? 1 : 0;
     ctl.spin_limit = 64;  // a few tens of microseconds
     ctl.nsteps = 2;
+    if (h->aa) {
+        // every counter at zero and the work counter past every job of
+        // sub-step 0: each job taken belongs to sub-step 1 and waits
+        const AAPlan a = aa_plan(h, ctl.group);
+        ctl.radius = 1;
+        const unsigned start = (unsigned)(2 * (a.items + a.lag));
+        cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)4 * (size_t)(1 + 2 * a.items), s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sync, &start, sizeof(unsigned), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = aa_launch(h, ctl, (int)a.lag, (int)std::min<int64_t>(h->ctas_max, (a.items + h->warps - 1) / h->warps), s);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "self-test launch");
+        return lbm_check(h, flags);
+    }
     // every counter at zero and the work counter past sub-step 0: each item
     // taken belongs to sub-step 1 and waits for a sub-step that never runs
     cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)4 * (size_t)(1 + items), s);
@@ -815,6 +920,22 @@ int lbm_set_item_group(lbm_lattice *h, int32_t group)
 }
 
 int32_t lbm_get_item_group(const lbm_lattice *h) { return valid(h) ? item_group(h) : -1; }
+
+int lbm_set_aa_lag(lbm_lattice *h, int32_t lag)
+{
+    if (!valid(h) || !h->aa || lag < 0)
+        return fail(LBM_ERR_INVALID_ARG, "bad handle, not an AA-pattern lattice, or negative lag");
+    h->lag = lag;
+    return LBM_OK;
+}
+
+int32_t lbm_get_aa_lag(const lbm_lattice *h)
+{
+    if (!valid(h) || !h->aa)
+        return -1;
+    const AAPlan a = aa_plan(h, item_group(h));
+    return a.multi ? (int32_t)a.lag : 0;
+}
 
 int64_t lbm_get_step(const lbm_lattice *h) { return valid(h) ? h->step : -1; }
 
@@ -886,6 +1007,15 @@ int lbm_get_state(lbm_lattice *h, double *dev_f, double *dev_g, lbm_stream strea
     const lbm_desc &d = h->d;
     const void *b = h->buf(h->cur);
     cudaError_t e;
+    if (h->aa) {
+        switch (d.storage) {
+        case LBM_F64: e = lbm::launch_aa_state_out_f64(b, h->phase, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+        case LBM_F32: e = lbm::launch_aa_state_out_f32(b, h->phase, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+        case LBM_F16: e = lbm::launch_aa_state_out_f16(b, h->phase, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+        default: e = lbm::launch_aa_state_out_bf16(b, h->phase, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+        }
+        return e == cudaSuccess ? LBM_OK : cuda_fail(e, "state read kernel launch");
+    }
     switch (d.storage) {
     case LBM_F64: e = lbm::launch_state_out_f64(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
     case LBM_F32: e = lbm::launch_state_out_f32(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
@@ -903,11 +1033,21 @@ int lbm_set_state(lbm_lattice *h, const double *dev_f, const double *dev_g, int6
     const lbm_desc &d = h->d;
     void *b = h->buf(h->cur);
     cudaError_t e;
-    switch (d.storage) {
-    case LBM_F64: e = lbm::launch_state_in_f64(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
-    case LBM_F32: e = lbm::launch_state_in_f32(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
-    case LBM_F16: e = lbm::launch_state_in_f16(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
-    default: e = lbm::launch_state_in_bf16(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+    if (h->aa) {  // written in representation 0
+        switch (d.storage) {
+        case LBM_F64: e = lbm::launch_aa_state_in_f64(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+        case LBM_F32: e = lbm::launch_aa_state_in_f32(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+        case LBM_F16: e = lbm::launch_aa_state_in_f16(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+        default: e = lbm::launch_aa_state_in_bf16(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+        }
+        h->phase = 0;
+    } else {
+        switch (d.storage) {
+        case LBM_F64: e = lbm::launch_state_in_f64(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+        case LBM_F32: e = lbm::launch_state_in_f32(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+        case LBM_F16: e = lbm::launch_state_in_f16(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+        default: e = lbm::launch_state_in_bf16(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+        }
     }
     if (e != cudaSuccess)
         return cuda_fail(e, "state write kernel launch");
@@ -926,15 +1066,22 @@ int lbm_checkpoint_bytes(const lbm_lattice *h, size_t *bytes)
     return LBM_OK;
 }
 
-// one strided copy per plane between the padded buffer and a dense [q][j][i] array
+// one strided copy per plane between the padded buffer and a dense [q][j][i]
+// array of post-collision values: plane q at its nodes (two buffers), or
+// in the AA pattern the window of the representation's plane that holds
+// population q of every node (lbm::aa_post_cell; restores write
+// representation 0)
 static int copy_planes(lbm_lattice *h, void *dense, bool out, cudaStream_t s)
 {
     const size_t es = storage_bytes(h->d.storage);
     const size_t row = (size_t)h->d.nx * es;
     const size_t pitch = (size_t)h->L.pitch * es;
     char *buf = static_cast<char *>(h->buf(h->cur));
+    const int phase = h->aa && out ? h->phase : 0;
     for (int q = 0; q < 13; ++q) {
-        char *padded = buf + ((size_t)q * (size_t)h->L.plane + (size_t)h->L.pitch + (size_t)lbm::PAD_COLS) * es;
+        const int64_t first = h->aa ? lbm::aa_post_cell(phase, q, 0, 0, h->L.pitch, h->L.plane)
+                                    : (int64_t)q * h->L.plane + h->L.pitch + lbm::PAD_COLS;
+        char *padded = buf + (size_t)first * es;
         char *flat = static_cast<char *>(dense) + (size_t)q * (size_t)h->d.nr * row;
         cudaError_t e = out ? cudaMemcpy2DAsync(flat, row, padded, pitch, row, h->d.nr, cudaMemcpyDeviceToDevice, s)
                             : cudaMemcpy2DAsync(padded, pitch, flat, row, row, h->d.nr, cudaMemcpyDeviceToDevice, s);
@@ -959,6 +1106,7 @@ int lbm_restore(lbm_lattice *h, const void *dev_in, int64_t step, lbm_stream str
     int rc = copy_planes(h, const_cast<void *>(dev_in), false, s);
     if (rc != LBM_OK)
         return rc;
+    h->phase = 0;
     h->step = step;
     h->prev_valid = false;
     if (h->batch)
@@ -1036,6 +1184,8 @@ int lbm_batch_add(lbm_batch *b, lbm_lattice *h)
         return fail(LBM_ERR_INVALID_ARG, "the lattice already belongs to a batch");
     if (h->d.storage != b->storage)
         return fail(LBM_ERR_INVALID_ARG, "storage type %d differs from the batch's %d", h->d.storage, b->storage);
+    if (h->aa)
+        return fail(LBM_ERR_INVALID_ARG, "AA-pattern lattices are stepped alone, not in batches");
     b->members.push_back(h);
     h->batch = b;
     b->dirty = true;

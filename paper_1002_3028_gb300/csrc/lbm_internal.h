@@ -6,12 +6,13 @@
 #include <stdint.h>
 
 #include "lbm.h"
-#include "lbm_kernels.cuh"
+#include "lbm_aa.cuh"
 
 namespace lbm {
 
-// Launchers, one set per storage type (defined in lbm_step_<type>.cu).
-// Each returns the cudaError_t of the launch.
+// Launchers, one set per storage type (defined in lbm_step_<type>.cu);
+// the aa_ ones are for lattices in the AA layout (lbm_aa.cuh).  Each
+// returns the cudaError_t of the launch.
 #define LBM_DECLARE_LAUNCHERS(TAG, C)                                                                  \
     cudaError_t launch_run_##TAG(const StepParams<C> &p, const RunCtl &ctl, int warps_per_cta, int ctas,  \
                                  cudaStream_t s);                                                      \
@@ -26,7 +27,15 @@ namespace lbm {
     cudaError_t launch_state_in_##TAG(void *buf, const double *f, const double *g, int nx, int nr,     \
                                       int pitch, int64_t plane, double rho0, double T0, cudaStream_t s); \
     cudaError_t launch_state_out_##TAG(const void *buf, double *f, double *g, int nx, int nr, int pitch, \
-                                       int64_t plane, double rho0, double T0, cudaStream_t s);
+                                       int64_t plane, double rho0, double T0, cudaStream_t s);            \
+    cudaError_t launch_aa_run_##TAG(const StepParams<C> &p, const RunCtl &ctl, int lag, int warps_per_cta, \
+                                    int ctas, cudaStream_t s);                                          \
+    cudaError_t occupancy_aa_run_##TAG(int warps_per_cta, int *ctas_per_sm);                           \
+    cudaError_t launch_aa_fill_##TAG(const StepParams<C> &p, cudaStream_t s);                          \
+    cudaError_t launch_aa_state_in_##TAG(void *buf, const double *f, const double *g, int nx, int nr,  \
+                                         int pitch, int64_t plane, double rho0, double T0, cudaStream_t s); \
+    cudaError_t launch_aa_state_out_##TAG(const void *buf, int phase, double *f, double *g, int nx, int nr, \
+                                          int pitch, int64_t plane, double rho0, double T0, cudaStream_t s);
 
 constexpr int DIAG_MAX_BLOCKS = 1024;  // partial-sum blocks of the diagnostics reduction
 

@@ -60,6 +60,13 @@ __host__ __device__ constexpr int ey9(int k) { return (k == 2 || k == 5 || k == 
 __host__ __device__ constexpr int ex4(int k) { return k == 0 ? 1 : (k == 2 ? -1 : 0); }
 __host__ __device__ constexpr int ey4(int k) { return k == 1 ? 1 : (k == 3 ? -1 : 0); }
 template <class C> __host__ __device__ constexpr C w9(int k) { return k == 0 ? C(4) / C(9) : (k <= 4 ? C(1) / C(9) : C(1) / C(36)); }
+// plane q = 0..12: f_0..f_8, then g_0..g_3; its velocity and the plane of the opposite velocity
+__host__ __device__ constexpr int qex(int q) { return q < 9 ? ex9(q) : ex4(q - 9); }
+__host__ __device__ constexpr int qey(int q) { return q < 9 ? ey9(q) : ey4(q - 9); }
+__host__ __device__ constexpr int opp_plane(int q)
+{
+    return q == 0 ? 0 : (q < 5 ? 1 + (q + 1) % 4 : (q < 9 ? 5 + (q - 3) % 4 : 9 + (q - 7) % 4));
+}
 
 // nodes per lane of the step kernel for an arithmetic type
 template <class C> struct NodesPerLane { static constexpr int value = 1; };
@@ -89,6 +96,9 @@ struct alignas(16) StepParams {
     const C *u_in, *T_in;         // inlet profiles, nr values
     const C *nu_tab, *al_tab;     // property tables, ntab values
     int *status;                  // error flags of the lattice
+    C *mom;                       // AA layout: 4 planes of the last step's moments (see lbm_aa.cuh)
+    int aa;                       // 1: one buffer in the AA layout (src == dst); 0: two buffers
+    int phase;                    // AA layout: representation of the stored state
 };
 
 // ---- storage conversions -----------------------------------------------------
@@ -236,23 +246,18 @@ __device__ __forceinline__ C feq_unit(int k, C ux, C ur)
 }
 
 // ---- boundary ghosts -------------------------------------------------------------
-// Node (i, j) on the lattice edge, whose post-collision deviations are
-// already stored in buf, writes every ghost cell of buf whose value the
-// boundary rules take from it.  t is the time index of the step that will
-// pull these ghosts (inlet noise).  Writers of distinct ghost cells are
-// distinct nodes, except where two rules give the same bounce-back value to
-// the same cell.
-template <class S, class C>
-__device__ __noinline__ void write_ghosts(const StepParams<C> &p, S *buf, int i, int j, int64_t t)
+// The boundary rules of node (i, j) on the lattice edge, given its
+// post-collision deviations fo, go: W(q, ci, cj, v) is called for every
+// ghost cell (ci, cj) of plane q whose value the rules take from this node
+// (v is that value).  t is the time index of the step that will pull these
+// ghosts (inlet noise).  Writers of distinct ghost cells are distinct
+// nodes, except where two rules give the same bounce-back value to the same
+// cell.
+template <class C, class Wr>
+__device__ __forceinline__ void ghost_rules(const StepParams<C> &p, const C (&fo)[9], const C (&go)[4], int i, int j,
+                                            int64_t t, Wr W)
 {
     const int nx = p.nx, nr = p.nr;
-    C fo[9], go[4];
-#pragma unroll
-    for (int k = 0; k < 9; ++k)
-        fo[k] = load_as_shared<S, C>(buf + cell(p, k, i, j));  // plain load: this thread stored it
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        go[k] = load_as_shared<S, C>(buf + cell(p, 9 + k, i, j));
     C drho = C(0), jx = C(0), jr = C(0);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -262,7 +267,6 @@ __device__ __noinline__ void write_ghosts(const StepParams<C> &p, S *buf, int i,
     }
     const C rho = p.rho0 + drho;
     const C ux = jx / rho, ur = jr / rho;
-    auto W = [&](int q, int ci, int cj, C v) { buf[cell(p, q, ci, cj)] = store_as<S, C>(v); };
     // zero-gradient copy of this node held at rho0
     auto openc = [&](int k) -> C { return fo[k] - drho * feq_unit<C>(k, ux, ur); };
     // inlet equilibrium at this node's density, this row's prescribed velocity
@@ -357,16 +361,43 @@ __device__ __noinline__ void write_ghosts(const StepParams<C> &p, S *buf, int i,
     }
 }
 
+// Two-buffer layout: node (i, j) on the lattice edge, whose post-collision
+// deviations are already stored in buf, writes the ghost cells of buf that
+// the rules take from it.
+template <class S, class C>
+__device__ __noinline__ void write_ghosts(const StepParams<C> &p, S *buf, int i, int j, int64_t t)
+{
+    C fo[9], go[4];
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+        fo[k] = load_as_shared<S, C>(buf + cell(p, k, i, j));  // plain load: this thread stored it
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        go[k] = load_as_shared<S, C>(buf + cell(p, 9 + k, i, j));
+    ghost_rules<C>(p, fo, go, i, j, t, [&](int q, int ci, int cj, C v) { buf[cell(p, q, ci, cj)] = store_as<S, C>(v); });
+}
+
 // ---- pull and moments -------------------------------------------------------------
+// element offset of population q streamed into node (i, j) from a stored
+// state: the post-collision value of node (i, j) - e_q (two buffers), or
+// the AA layout's slot for that population in the state's representation
+template <class C>
+__device__ __forceinline__ int64_t stream_cell(const StepParams<C> &p, int q, int i, int j)
+{
+    if (p.aa && p.phase)
+        return cell(p, q, i, j);
+    return cell(p, p.aa ? opp_plane(q) : q, i - qex(q), j - qey(q));
+}
+
 template <class S, class C>
 __device__ __forceinline__ void pull(const StepParams<C> &p, const S *src, int i, int j, C (&f)[9], C (&g)[4])
 {
 #pragma unroll
     for (int k = 0; k < 9; ++k)
-        f[k] = ld<S, C>(p, src, k, i - ex9(k), j - ey9(k));
+        f[k] = load_as<S, C>(src + stream_cell(p, k, i, j));
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-        g[k] = ld<S, C>(p, src, 9 + k, i - ex4(k), j - ey4(k));
+        g[k] = load_as<S, C>(src + stream_cell(p, 9 + k, i, j));
 }
 
 template <class V>
@@ -408,6 +439,34 @@ __device__ __forceinline__ Mom<V> ghost_top(const StepParams<C> &p, Mom<V> m)
         m.dT = V(C(2) * p.dT_top) - m.dT;
     }
     return m;
+}
+
+// Eq. 2 moments at node (i, j) (deviations from rest) of the populations
+// streamed from the stored state, or (previous) of the step before: from
+// the other buffer (two-buffer layout) or the stored moment planes (AA)
+template <class S, class C>
+__device__ __forceinline__ Mom<Vec<C, 1>> node_moments(const StepParams<C> &p, int i, int j, bool previous)
+{
+    using V1 = Vec<C, 1>;
+    if (previous && p.aa) {
+        const int64_t o = cell(p, 0, i, j);
+        Mom<V1> m;
+        m.drho = V1(__ldcg(p.mom + o));
+        m.jx = V1(__ldcg(p.mom + p.plane + o));
+        m.jr = V1(__ldcg(p.mom + 2 * p.plane + o));
+        m.dT = V1(__ldcg(p.mom + 3 * p.plane + o));
+        return m;
+    }
+    C f[9], g[4];
+    pull<S, C>(p, static_cast<const S *>(previous ? p.dst : p.src), i, j, f, g);
+    V1 vf[9], vg[4];
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+        vf[k] = V1(f[k]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        vg[k] = V1(g[k]);
+    return moments<V1>(vf, vg);
 }
 
 // rho u_r of the streamed populations at lattice node (i, j): the six
@@ -695,12 +754,11 @@ __device__ __forceinline__ CopyPlan<S, NV> make_copy_plan(const StepParams<C> &p
     return cp;
 }
 
-// start the copies of lattice row r into one stage
-template <class S, int NV, class C>
-__device__ __forceinline__ void issue_row(const StepParams<C> &p, const S *src, S *stage, const CopyPlan<S, NV> &cp,
-                                          int r, int lane)
+// start the copies of lattice row r into one stage (CP: a copy plan with
+// the members of CopyPlan)
+template <class S, int NV, class C, class CP>
+__device__ __forceinline__ void issue_row(const StepParams<C> &p, const S *src, S *stage, const CP &cp, int r, int lane)
 {
-    using CP = CopyPlan<S, NV>;
     const int row = (r + 1) * p.pitch;
 #pragma unroll
     for (int m = 0; m < CP::PER_LANE; ++m) {
@@ -1112,17 +1170,7 @@ __global__ void fields_kernel(const __grid_constant__ StepParams<C> p, O *out)
     if (n >= N)
         return;
     const int i = (int)(n % p.nx), j = (int)(n / p.nx);
-    const S *src = static_cast<const S *>(p.src);
-    C f[9], g[4];
-    pull<S, C>(p, src, i, j, f, g);
-    Vec<C, 1> vf[9], vg[4];
-#pragma unroll
-    for (int k = 0; k < 9; ++k)
-        vf[k] = Vec<C, 1>(f[k]);
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        vg[k] = Vec<C, 1>(g[k]);
-    const Mom<Vec<C, 1>> m = moments<Vec<C, 1>>(vf, vg);
+    const Mom<Vec<C, 1>> m = node_moments<S, C>(p, i, j, false);
     const C rho = p.rho0 + m.drho.x;
     out[n] = O(rho);
     out[N + n] = O(m.jx.x / rho);
@@ -1131,8 +1179,8 @@ __global__ void fields_kernel(const __grid_constant__ StepParams<C> p, O *out)
 }
 
 // ---- FP64 diagnostics: mass, heat, steady residual, divergence -------------------------
-// Per node, from the populations streamed from the current state (and from
-// the previous state in the other buffer): rho, u, T of Eq. 2.  Sums run in
+// Per node, from the populations streamed from the current state (and the
+// moments of the previous step): rho, u, T of Eq. 2.  Sums run in
 // FP64: Σ rho, Σ r rho, Σ T, Σ r T, Σ |u(t) - u(t-1)|^2, Σ |u(t)|^2,
 // max |u(t) - u(t-1)|, max |u(t)|, and the count of nodes whose rho is not
 // finite and positive or whose T is not finite.  Block partials go to
@@ -1170,52 +1218,43 @@ __device__ __forceinline__ void diag_block_reduce(double (&v)[DIAG_SLOTS])
             diag_combine(v, sh[w]);
 }
 
+// adds node (i, j) to the per-thread slots
+template <class S, class C>
+__device__ __forceinline__ void diag_node(const StepParams<C> &p, int have_prev, int i, int j, double (&v)[DIAG_SLOTS])
+{
+    const Mom<Vec<C, 1>> m = node_moments<S, C>(p, i, j, false);
+    const double rho = (double)p.rho0 + (double)m.drho.x;
+    const double T = (double)p.T0 + (double)m.dT.x;
+    const double ux = (double)m.jx.x / rho, ur = (double)m.jr.x / rho;
+    const double r = (double)p.r0 + j + 0.5;
+    if (!(rho > 0.0) || !isfinite(rho) || !isfinite(T) || !isfinite(ux) || !isfinite(ur)) {
+        v[7] += 1.0;
+        return;
+    }
+    v[0] += rho;
+    v[1] += r * rho;
+    v[2] += T;
+    v[3] += r * T;
+    const double uu = ux * ux + ur * ur;
+    v[8] += uu;
+    v[6] = fmax(v[6], sqrt(uu));
+    if (have_prev) {
+        const Mom<Vec<C, 1>> q = node_moments<S, C>(p, i, j, true);
+        const double rp = (double)p.rho0 + (double)q.drho.x;
+        const double dx = ux - (double)q.jx.x / rp, dr = ur - (double)q.jr.x / rp;
+        v[4] += dx * dx + dr * dr;
+        v[5] = fmax(v[5], sqrt(dx * dx + dr * dr));
+    }
+}
+
 template <class S, class C>
 __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const __grid_constant__ StepParams<C> p, int have_prev,
                                                             double *partials)
 {
     double v[DIAG_SLOTS] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     const int64_t N = (int64_t)p.nx * p.nr;
-    const S *cur = static_cast<const S *>(p.src);
-    const S *prev = static_cast<const S *>(p.dst);
-    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(n % p.nx), j = (int)(n / p.nx);
-        C f[9], g[4];
-        pull<S, C>(p, cur, i, j, f, g);
-        Vec<C, 1> vf[9], vg[4];
-        for (int k = 0; k < 9; ++k)
-            vf[k] = Vec<C, 1>(f[k]);
-        for (int k = 0; k < 4; ++k)
-            vg[k] = Vec<C, 1>(g[k]);
-        const Mom<Vec<C, 1>> m = moments<Vec<C, 1>>(vf, vg);
-        const double rho = (double)p.rho0 + (double)m.drho.x;
-        const double T = (double)p.T0 + (double)m.dT.x;
-        const double ux = (double)m.jx.x / rho, ur = (double)m.jr.x / rho;
-        const double r = (double)p.r0 + j + 0.5;
-        if (!(rho > 0.0) || !isfinite(rho) || !isfinite(T) || !isfinite(ux) || !isfinite(ur)) {
-            v[7] += 1.0;
-            continue;
-        }
-        v[0] += rho;
-        v[1] += r * rho;
-        v[2] += T;
-        v[3] += r * T;
-        const double uu = ux * ux + ur * ur;
-        v[8] += uu;
-        v[6] = fmax(v[6], sqrt(uu));
-        if (have_prev) {
-            pull<S, C>(p, prev, i, j, f, g);
-            for (int k = 0; k < 9; ++k)
-                vf[k] = Vec<C, 1>(f[k]);
-            for (int k = 0; k < 4; ++k)
-                vg[k] = Vec<C, 1>(g[k]);
-            const Mom<Vec<C, 1>> q = moments<Vec<C, 1>>(vf, vg);
-            const double rp = (double)p.rho0 + (double)q.drho.x;
-            const double dx = ux - (double)q.jx.x / rp, dr = ur - (double)q.jr.x / rp;
-            v[4] += dx * dx + dr * dr;
-            v[5] = fmax(v[5], sqrt(dx * dx + dr * dr));
-        }
-    }
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+        diag_node<S, C>(p, have_prev, (int)(n % p.nx), (int)(n / p.nx), v);
     diag_block_reduce(v);
     if (threadIdx.x == 0)
         for (int k = 0; k < DIAG_SLOTS; ++k)

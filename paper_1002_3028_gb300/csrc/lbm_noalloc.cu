@@ -44,9 +44,9 @@ int scratch_on(int device, double **ptr)
     return LBM_OK;
 }
 
-// One CTA per lattice row: the row's nodes, streamed from the current state
-// (and from the previous state in the other buffer), reduced in FP64 into
-// the row's DIAG_SLOTS partial slots; same per-node quantities as the
+// One CTA per lattice row: the row's nodes (populations streamed from the
+// current state, moments of the previous step) reduced in FP64 into the
+// row's DIAG_SLOTS partial slots; same per-node quantities as the
 // lattice-scratch diagnostics.
 template <class S, class C>
 __global__ void __launch_bounds__(DIAG_THREADS) diag_rows_kernel(const __grid_constant__ StepParams<C> p,
@@ -54,45 +54,8 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_rows_kernel(const __grid_co
 {
     double v[DIAG_SLOTS] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     const int j = blockIdx.x;
-    const S *cur = static_cast<const S *>(p.src);
-    const S *prev = static_cast<const S *>(p.dst);
-    const double r = (double)p.r0 + j + 0.5;
-    for (int i = threadIdx.x; i < p.nx; i += blockDim.x) {
-        C f[9], g[4];
-        pull<S, C>(p, cur, i, j, f, g);
-        Vec<C, 1> vf[9], vg[4];
-        for (int k = 0; k < 9; ++k)
-            vf[k] = Vec<C, 1>(f[k]);
-        for (int k = 0; k < 4; ++k)
-            vg[k] = Vec<C, 1>(g[k]);
-        const Mom<Vec<C, 1>> m = moments<Vec<C, 1>>(vf, vg);
-        const double rho = (double)p.rho0 + (double)m.drho.x;
-        const double T = (double)p.T0 + (double)m.dT.x;
-        const double ux = (double)m.jx.x / rho, ur = (double)m.jr.x / rho;
-        if (!(rho > 0.0) || !isfinite(rho) || !isfinite(T) || !isfinite(ux) || !isfinite(ur)) {
-            v[7] += 1.0;
-            continue;
-        }
-        v[0] += rho;
-        v[1] += r * rho;
-        v[2] += T;
-        v[3] += r * T;
-        const double uu = ux * ux + ur * ur;
-        v[8] += uu;
-        v[6] = fmax(v[6], sqrt(uu));
-        if (have_prev) {
-            pull<S, C>(p, prev, i, j, f, g);
-            for (int k = 0; k < 9; ++k)
-                vf[k] = Vec<C, 1>(f[k]);
-            for (int k = 0; k < 4; ++k)
-                vg[k] = Vec<C, 1>(g[k]);
-            const Mom<Vec<C, 1>> q = moments<Vec<C, 1>>(vf, vg);
-            const double rp = (double)p.rho0 + (double)q.drho.x;
-            const double dx = ux - (double)q.jx.x / rp, dr = ur - (double)q.jr.x / rp;
-            v[4] += dx * dx + dr * dr;
-            v[5] = fmax(v[5], sqrt(dx * dx + dr * dr));
-        }
-    }
+    for (int i = threadIdx.x; i < p.nx; i += blockDim.x)
+        diag_node<S, C>(p, have_prev, i, j, v);
     diag_block_reduce(v);
     if (threadIdx.x == 0)
         for (int k = 0; k < DIAG_SLOTS; ++k)

@@ -109,4 +109,53 @@ cudaError_t LBM_CAT(launch_state_out_, LBM_TAG)(const void *buf, double *f, doub
     return cudaGetLastError();
 }
 
+// ---- AA layout ------------------------------------------------------------------------
+cudaError_t LBM_CAT(launch_aa_run_, LBM_TAG)(const StepParams<LBM_C> &p, const RunCtl &ctl, int lag, int warps_per_cta,
+                                             int ctas, cudaStream_t s)
+{
+    if (p.ntiles <= 0 || ctl.nsteps <= 0)
+        return cudaSuccess;
+    const int smem = run_smem<LBM_S, LBM_C>(warps_per_cta);
+    aa_run_kernel<LBM_S, LBM_C><<<ctas, 32 * warps_per_cta, smem, s>>>(p, ctl, lag);
+    return cudaGetLastError();
+}
+
+cudaError_t LBM_CAT(occupancy_aa_run_, LBM_TAG)(int warps_per_cta, int *ctas_per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute(aa_run_kernel<LBM_S, LBM_C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         run_smem<LBM_S, LBM_C>(8));
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, aa_run_kernel<LBM_S, LBM_C>, 32 * warps_per_cta,
+                                                         run_smem<LBM_S, LBM_C>(warps_per_cta));
+}
+
+cudaError_t LBM_CAT(launch_aa_fill_, LBM_TAG)(const StepParams<LBM_C> &p, cudaStream_t s)
+{
+    const int64_t N = (int64_t)p.nx * p.nr;
+    const int threads = 256;
+    aa_fill_ghosts_kernel<LBM_S, LBM_C><<<(unsigned)((N + threads - 1) / threads), threads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t LBM_CAT(launch_aa_state_in_, LBM_TAG)(void *buf, const double *f, const double *g, int nx, int nr,
+                                                  int pitch, int64_t plane, double rho0, double T0, cudaStream_t s)
+{
+    const int64_t n = 13 * (int64_t)nx * nr;
+    const int threads = 256;
+    aa_state_in_kernel<LBM_S><<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(
+        static_cast<LBM_S *>(buf), f, g, nx, nr, pitch, plane, rho0, T0);
+    return cudaGetLastError();
+}
+
+cudaError_t LBM_CAT(launch_aa_state_out_, LBM_TAG)(const void *buf, int phase, double *f, double *g, int nx, int nr,
+                                                   int pitch, int64_t plane, double rho0, double T0, cudaStream_t s)
+{
+    const int64_t n = 13 * (int64_t)nx * nr;
+    const int threads = 256;
+    aa_state_out_kernel<LBM_S><<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(
+        static_cast<const LBM_S *>(buf), phase, f, g, nx, nr, pitch, plane, rho0, T0);
+    return cudaGetLastError();
+}
+
 }  // namespace lbm

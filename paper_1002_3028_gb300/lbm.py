@@ -25,6 +25,7 @@ _BC_IN = {"inlet": 0, "periodic": 1}
 _BC_OUT = {"outflow": 0, "wall": 1, "periodic": 2}
 _BC_TOP = {"wall": 0, "open": 1}
 _BC_BOTTOM = {"axis": 0, "wall": 1}
+PATTERN = {"ab": 0, "aa": 1}
 
 HEADER = os.path.join(_build.ROOT, "include", "lbm.h")
 
@@ -44,7 +45,7 @@ class Desc(C.Structure):
         ("axisym", C.c_int32),
         ("r0", C.c_double), ("rho0", C.c_double), ("T0", C.c_double), ("Cs", C.c_double),
         ("Pr_t", C.c_double), ("T_top", C.c_double), ("T_bottom", C.c_double), ("T_out", C.c_double),
-        ("noise_amp", C.c_double), ("seed", C.c_uint64),
+        ("noise_amp", C.c_double), ("seed", C.c_uint64), ("pattern", C.c_int32),
     ]
 
 
@@ -59,8 +60,8 @@ class Diag(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
-def make_desc(cfg: LatticeConfig, storage: str) -> Desc:
-    return Desc(nx=cfg.nx, nr=cfg.nr, storage=STORAGE[storage], bc_in=_BC_IN[cfg.bc_in],
+def make_desc(cfg: LatticeConfig, storage: str, pattern: str = "ab") -> Desc:
+    return Desc(pattern=PATTERN[pattern], nx=cfg.nx, nr=cfg.nr, storage=STORAGE[storage], bc_in=_BC_IN[cfg.bc_in],
                 bc_out=_BC_OUT[cfg.bc_out], bc_top=_BC_TOP[cfg.bc_top],
                 bc_bottom=_BC_BOTTOM[cfg.bc_bottom], axisym=int(cfg.axisym), r0=cfg.r0,
                 rho0=cfg.rho0, T0=cfg.T0, Cs=cfg.Cs, Pr_t=cfg.Pr_t, T_top=cfg.T_top,
@@ -112,6 +113,9 @@ def lib(build: bool = True):
             L.lbm_selftest_wait_timeout.argtypes = [vp, C.POINTER(i32)]
             L.lbm_get_item_group.restype = i32
             L.lbm_get_item_group.argtypes = [vp]
+            L.lbm_set_aa_lag.argtypes = [vp, i32]
+            L.lbm_get_aa_lag.restype = i32
+            L.lbm_get_aa_lag.argtypes = [vp]
             L.lbm_check.argtypes = [vp, C.POINTER(i32)]
             L.lbm_diagnostics.argtypes = [vp, C.POINTER(Diag), vp]
             L.lbm_diagnostics_noalloc.argtypes = [vp, C.POINTER(Diag), vp]
@@ -129,7 +133,7 @@ def lib(build: bool = True):
                          "lbm_step", "lbm_get_fields", "lbm_get_state", "lbm_set_state",
                          "lbm_set_launch", "lbm_get_launch", "lbm_check", "lbm_batch_create",
                          "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_set_launch",
-                         "lbm_batch_get_launch", "lbm_diagnostics", "lbm_diagnostics_noalloc"):
+                         "lbm_batch_get_launch", "lbm_diagnostics", "lbm_diagnostics_noalloc", "lbm_set_aa_lag"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -140,8 +144,8 @@ def _check(rc: int, what: str):
         raise LbmError(rc, what, lib().lbm_last_error().decode())
 
 
-def required_bytes(cfg: LatticeConfig, storage: str = "f32") -> int:
-    d = make_desc(cfg, storage)
+def required_bytes(cfg: LatticeConfig, storage: str = "f32", pattern: str = "ab") -> int:
+    d = make_desc(cfg, storage, pattern)
     n = C.c_size_t(0)
     _check(lib().lbm_required_bytes(C.byref(d), C.byref(n)), "lbm_required_bytes")
     return int(n.value)
@@ -159,21 +163,28 @@ def _dptr(a):
 
 
 class Lattice:
-    """One lattice resident on the GPU, advanced by the fused CUDA step."""
+    """One lattice resident on the GPU, advanced by the fused CUDA step.
 
-    def __init__(self, cfg: LatticeConfig, storage: str = "f32", device=None):
+    ``pattern`` is the memory layout: "ab" (two population buffers) or "aa"
+    (one buffer updated in place, plus the moment planes; same results).
+    """
+
+    def __init__(self, cfg: LatticeConfig, storage: str = "f32", device=None, pattern: str = "ab"):
         import torch
 
         cfg.validate()
         if storage not in STORAGE:
             raise ValueError(f"storage must be one of {sorted(STORAGE)}")
+        if pattern not in PATTERN:
+            raise ValueError(f"pattern must be one of {sorted(PATTERN)}")
         self.cfg = cfg
         self.storage = storage
+        self.pattern = pattern
         self.nx, self.nr = cfg.nx, cfg.nr
         self.device = torch.device(device if device is not None else "cuda")
         self._L = lib()
-        self._desc = make_desc(cfg, storage)
-        self.nbytes = required_bytes(cfg, storage)
+        self._desc = make_desc(cfg, storage, pattern)
+        self.nbytes = required_bytes(cfg, storage, pattern)
         with torch.cuda.device(self.device):
             # the caching allocator hands out 512-byte aligned blocks
             self._mem = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
@@ -183,8 +194,8 @@ class Lattice:
         self._h = h
 
     @classmethod
-    def from_workload(cls, w: Workload, storage: str = "f32", device=None) -> "Lattice":
-        lat = cls(w.cfg, storage, device)
+    def from_workload(cls, w: Workload, storage: str = "f32", device=None, pattern: str = "ab") -> "Lattice":
+        lat = cls(w.cfg, storage, device, pattern)
         lat.set_inlet(w.u_in, w.T_in)
         lat.set_properties(w.nu_tab, w.alpha_tab, w.T_lo, w.T_hi)
         return lat
@@ -234,6 +245,15 @@ class Lattice:
     @property
     def item_group(self) -> int:
         return int(self._L.lbm_get_item_group(self._h))
+
+    def set_aa_lag(self, lag: int = 0):
+        """AA pattern: lag of the collision pass in work items (0 = automatic)."""
+        _check(self._L.lbm_set_aa_lag(self._h, int(lag)), "lbm_set_aa_lag")
+
+    @property
+    def aa_lag(self) -> int:
+        """Lag lbm_step uses (0: one step per launch; -1: not an AA lattice)."""
+        return int(self._L.lbm_get_aa_lag(self._h))
 
     def launch(self):
         """(band rows, warps per CTA, CTAs) used by lbm_step."""
