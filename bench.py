@@ -33,8 +33,21 @@ if ROOT not in sys.path:
 
 BYTES_PER_VALUE = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 POPS = 13  # 9 D2Q9 + 4 D2Q4 populations, each read once and written once per update
+
+
+def bytes_per_lup(storage: str) -> int:
+    """Algorithmic DRAM bytes per lattice update, either pattern: every population read
+    once and written once (the AA pattern's edge moments are a few per cent more and are
+    not counted)."""
+    return POPS * 2 * BYTES_PER_VALUE[storage]
+
+
+def resident_mb(storage: str, pattern: str, nodes: int) -> float:
+    """Population storage of the lattices (one buffer for the AA pattern, two otherwise), in MB."""
+    return POPS * BYTES_PER_VALUE[storage] * (1 if pattern == "aa" else 2) * nodes / 1e6
 METRIC = "MLUPS & HBM-roofline % (D2Q9+D2Q4 LES); serving p50/p99 latency vs plain"
 KERNEL_SRC = os.path.join(ROOT, "paper_1002_3028_gb300", "csrc", "lbm_kernels.cuh")
+AA_SRC = os.path.join(ROOT, "paper_1002_3028_gb300", "csrc", "lbm_aa.cuh")
 
 
 def workloads_by_name(name: str):
@@ -68,26 +81,30 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_hash() -> str:
+def kernel_hash(pattern: str = "ab") -> str:
     """First 16 hex digits of the SHA-256 of the kernel source's code: every line cut at `//`,
-    trailing blanks and empty lines dropped, so that comment edits keep the hash."""
-    with open(KERNEL_SRC) as fh:
-        lines = (ln.split("//", 1)[0].rstrip() for ln in fh.read().splitlines())
-    code = "\n".join(ln for ln in lines if ln)
-    return hashlib.sha256(code.encode()).hexdigest()[:16]
+    trailing blanks and empty lines dropped, so that comment edits keep the hash.  The AA
+    pattern's kernel also covers its own source file."""
+    code = []
+    for path in (KERNEL_SRC, AA_SRC) if pattern == "aa" else (KERNEL_SRC,):
+        with open(path) as fh:
+            lines = (ln.split("//", 1)[0].rstrip() for ln in fh.read().splitlines())
+        code.extend(ln for ln in lines if ln)
+    return hashlib.sha256("\n".join(code).encode()).hexdigest()[:16]
 
 
-def ncu_traffic(storage: str, workload: str):
+def ncu_traffic(storage: str, workload: str, pattern: str = "ab"):
     """DRAM bytes per step of the step kernel (a launch holds K steps; per step, like
     `achieved`) from the committed ncu summary, or None if there is none for this
-    storage/workload or the kernel source changed since."""
-    path = os.path.join(ROOT, "profiles", f"step_kernel_{storage}_{workload}.md")
+    storage/workload/pattern or the kernel source changed since."""
+    name = f"step_kernel_{storage}_{workload}.md" if pattern == "ab" else f"aa_step_kernel_{storage}_{workload}.md"
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     text = open(path).read()
     h = re.search(r"kernel_code_sha256_16:\s*([0-9a-f]+)", text)
     b = re.search(r"dram_bytes_per_step_full_size:\s*([0-9.eE+]+)", text)
-    if not h or not b or h.group(1) != kernel_hash():
+    if not h or not b or h.group(1) != kernel_hash(pattern):
         return None
     return float(b.group(1))
 
@@ -258,7 +275,7 @@ def run_reference(args):
     return 0
 
 
-def error_vs_f64(works, storage: str, device, steps: int = 1000, sample: int = 4):
+def error_vs_f64(works, storage: str, device, steps: int = 1000, sample: int = 4, pattern: str = "ab"):
     """Field errors of the measured storage type against the FP64 GPU path (which the parity
     tests hold to the oracle within 1e-12 per step): up to `sample` lattices of the workload
     run `steps` steps from the same start in both, and the largest relative errors of rho,
@@ -270,7 +287,7 @@ def error_vs_f64(works, storage: str, device, steps: int = 1000, sample: int = 4
     picks = list(range(0, len(works), max(1, len(works) // sample)))[:sample]
     worst = {"rho": 0.0, "u": 0.0, "T": 0.0}
     for k in picks:
-        a = lbm.Lattice.from_workload(works[k], storage, device=device)
+        a = lbm.Lattice.from_workload(works[k], storage, device=device, pattern=pattern)
         b = lbm.Lattice.from_workload(works[k], "f64", device=device)
         a.step(steps)
         b.step(steps)
@@ -287,8 +304,9 @@ def error_vs_f64(works, storage: str, device, steps: int = 1000, sample: int = 4
 
 def step_launches(lats, storage: str, launch, steps: int) -> int:
     """Kernels launched by `steps` steps.  One lattice runs its steps in persistent launches
-    of up to 2^31 / (2 x warp tiles) steps each.  A batch replays a captured launch of 64
-    steps and runs the rest in one launch; each launch is followed by the parameter advance."""
+    of up to 2^31 / (2 x warp tiles) steps each (either pattern).  A batch replays a
+    captured launch of 64 steps and runs the rest in one launch; each launch is followed
+    by the parameter advance."""
     strip = 32 if storage == "f64" else 64
     band = launch[0]
     ntiles = sum(-(-lat.nx // strip) * -(-lat.nr // band) for lat in lats)
@@ -311,7 +329,9 @@ def run_gpu(args):
 
     works = workloads_by_name(args.workload)
     label = workload_label(args.workload, works)
-    lats = [lbm.Lattice.from_workload(w, args.storage, device=device) for w in works]
+    if args.pattern == "aa" and len(works) > 1:
+        raise SystemExit("the AA pattern steps single lattices, not batches")
+    lats = [lbm.Lattice.from_workload(w, args.storage, device=device, pattern=args.pattern) for w in works]
     nodes = sum(w.nodes for w in works)
     stream = torch.cuda.current_stream(device)
     if len(lats) == 1:
@@ -349,7 +369,7 @@ def run_gpu(args):
     ms, units = replicas.combine(ev0.elapsed_time(ev1), nodes * args.steps, device)
     mlups = units / (ms * 1e-3) / 1e6
     per_step_s = ms * 1e-3 / args.steps
-    bpl = POPS * 2 * BYTES_PER_VALUE[args.storage]
+    bpl = bytes_per_lup(args.storage)
     achieved = bpl * nodes / per_step_s / 1e9  # algorithmic bytes of the launch(es) / their duration
     peak, peak_kind = measured_peaks()
     finite = all(bool(torch.isfinite(lat.fields(dtype=torch.float32)).all().item()) for lat in lats)
@@ -391,24 +411,26 @@ def run_gpu(args):
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
            "note": "initial states uploaded, K steps, fields downloaded; copies amortised over K"}
 
-    errors = error_vs_f64(works, args.storage, device)
+    errors = error_vs_f64(works, args.storage, device, pattern=args.pattern)
     if rank != 0:
         replicas.finish()
         return 0
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(works, args.cpu_seconds, label)
-    traffic = ncu_traffic(args.storage, args.workload)
+    traffic = ncu_traffic(args.storage, args.workload, args.pattern)
     launch = target.launch()
     line = {
         "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage != "f64" else "f64",
         "data": "synthetic",
-        "config": {"workload": label, "storage": args.storage, "nodes": nodes, "lattices": len(lats),
-                   "parallelism": f"replicas{ws}" if ws > 1 else "single",
-                   "l2": "no flush: inputs larger than L2 (two population buffers of "
-                         f"{2 * POPS * BYTES_PER_VALUE[args.storage] * nodes / 1e6:.0f} MB)",
+        "config": {"workload": label, "storage": args.storage, "pattern": args.pattern, "nodes": nodes,
+                   "lattices": len(lats), "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                   "l2": "no flush: inputs larger than L2 ("
+                         + ("one population buffer" if args.pattern == "aa"
+                            else "two population buffers")
+                         + f" of {resident_mb(args.storage, args.pattern, nodes):.0f} MB)",
                    "bytes_per_lup": bpl,
                    "launch": dict(zip(("band_rows", "warps_per_cta", "ctas" if len(lats) == 1 else "tiles"),
                                       launch))},
@@ -482,6 +504,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="jet4096x1024")
     ap.add_argument("--storage", default="f32", choices=sorted(BYTES_PER_VALUE))
+    ap.add_argument("--pattern", default="ab", choices=["ab", "aa"],
+                    help="memory layout: two population buffers, or one updated in place (AA)")
     ap.add_argument("--band", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--group", type=int, default=0,

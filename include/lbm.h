@@ -78,15 +78,17 @@ typedef enum { LBM_BOTTOM_AXIS = 0, LBM_BOTTOM_WALL = 1 } lbm_bc_bottom;
  *   LBM_PATTERN_AB  two buffers: each step pulls from one and writes the
  *                   other (the default).
  *   LBM_PATTERN_AA  one buffer updated in place (the "AA" pattern of
- *                   Bailey et al., ICPP 2009), plus 4 planes of the last
- *                   step's moments in the arithmetic type: 13 populations
- *                   + 4 moments per node instead of 26 populations (FP32:
- *                   68 instead of 104 bytes per node; FP16/BF16: 42
- *                   instead of 52; FP64: 136 instead of 208).  Each step is
- *                   two passes in one launch (moments, then collision; the
- *                   same-time neighbour moments of Eq. 1's sources need the
- *                   first).  Results are bit for bit those of LBM_PATTERN_AB.
- *                   Not for batch members. */
+ *                   Bailey et al., ICPP 2009), plus the moments at the warp
+ *                   tiles' edges that neighbouring tiles exchange within a
+ *                   step (the same-time neighbour moments of Eq. 1's
+ *                   sources): 13 populations and about 1.5 moment values
+ *                   per node instead of 26 populations (FP32: about 58
+ *                   instead of 104 bytes per node; FP16/BF16 about 32
+ *                   instead of 52; FP64 about 116 instead of 208).  Results
+ *                   are bit for bit those of LBM_PATTERN_AB, except that
+ *                   no previous state is kept (lbm_diagnostics reports no
+ *                   residual).  Bands are at least 4 rows.  Not for batch
+ *                   members. */
 typedef enum { LBM_PATTERN_AB = 0, LBM_PATTERN_AA = 1 } lbm_pattern;
 
 /*
@@ -171,9 +173,8 @@ LBM_API int lbm_set_properties(lbm_lattice *h, const double *nu, const double *a
 /*
  * Advance nsteps >= 0 time steps (Eq. 1).  All the steps run in one
  * persistent launch of the fused kernel (more than one only when nsteps x
- * warp tiles exceeds 2^30, or for small LBM_PATTERN_AA lattices, see
- * lbm_set_aa_lag): a warp tile of step t + 1 starts once the tiles around
- * it have finished step t.  The result is bit for bit that of nsteps
+ * warp tiles exceeds 2^30): a warp tile of step t + 1 starts once the tiles
+ * around it have finished step t.  The result is bit for bit that of nsteps
  * one-step calls.  Asynchronous; returns LBM_ERR_CUDA if a launch fails.  A
  * wait that runs out (it cannot in a correct launch; it is bounded all the
  * same) raises LBM_STATUS_TIMEOUT (see lbm_check) and ends the launch early.
@@ -191,7 +192,7 @@ LBM_API int64_t lbm_get_step(const lbm_lattice *h);
  * steady-state residual between the current and the previous step
  * (residual_max = max |u(t) - u(t-1)| / max |u(t)|, residual_l2 =
  * sqrt(Σ |u(t) - u(t-1)|^2 / Σ |u(t)|^2); NaN unless the last change of the
- * state was a step), and nonfinite = the number of nodes whose density is
+ * state was a step, and always NaN for LBM_PATTERN_AA), and nonfinite = the number of nodes whose density is
  * not finite and positive or whose velocity or temperature is not finite.
  * Uses the lattice's own scratch area; synchronises the stream and writes
  * *out.  Returns LBM_ERR_DIVERGED (with *out filled) when nonfinite > 0.
@@ -300,20 +301,11 @@ LBM_API int lbm_set_launch(lbm_lattice *h, int32_t band_rows, int32_t warps_per_
  * launch (any pointer may be NULL). */
 LBM_API int lbm_get_launch(const lbm_lattice *h, int32_t *band_rows, int32_t *warps_per_cta, int32_t *ctas);
 
-/* LBM_PATTERN_AA lattices: the lag of the collision pass behind the moments
- * pass in lbm_step's launch, in work items (0 = automatic: one band of
- * items plus half the warps resident at once).  It is clamped to the range
- * in which every wait is on earlier work; lattices with fewer than about
- * three bands of items run one step per launch instead.  Results do not
- * depend on it.  lbm_get_aa_lag returns the lag lbm_step uses (0 for one
- * step per launch, -1 for a bad handle or a two-buffer lattice). */
-LBM_API int lbm_set_aa_lag(lbm_lattice *h, int32_t lag);
-LBM_API int32_t lbm_get_aa_lag(const lbm_lattice *h);
-
 /* Work-item size of lbm_step's persistent launch: a warp takes `group`
  * adjacent warp tiles of one band at a time and synchronises with its
- * neighbours once per item (1..64; 0 = automatic).  Results do not depend
- * on it.  lbm_get_item_group returns the value in use (-1 for a bad handle). */
+ * neighbours once per item (1..64; 0 = automatic; LBM_PATTERN_AA lattices
+ * widen items where the GPU holds too few warps for one band of items).
+ * Results do not depend on it.  lbm_get_item_group returns the value in use (-1 for a bad handle). */
 LBM_API int lbm_set_item_group(lbm_lattice *h, int32_t group);
 LBM_API int32_t lbm_get_item_group(const lbm_lattice *h);
 

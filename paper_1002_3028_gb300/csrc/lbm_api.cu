@@ -64,7 +64,7 @@ struct Layout {
     int64_t plane;
     size_t buf_bytes;                    // one population buffer (13 planes)
     size_t off_buf[2];                   // the same buffer twice for the AA pattern
-    size_t off_mom;                      // AA pattern: 4 moment planes of the arithmetic type
+    size_t off_edge;                     // AA pattern: edge moments of the warp tiles (lbm_aa.cuh)
     size_t off_uin_d, off_tin_d, off_uin_f, off_tin_f;
     size_t off_nu_d, off_al_d, off_nu_f, off_al_f;
     size_t off_status;
@@ -116,8 +116,9 @@ Layout make_layout(const lbm_desc *d)
     o += L.buf_bytes;
     L.off_buf[1] = aa ? L.off_buf[0] : o;
     o += aa ? 0 : L.buf_bytes;
-    L.off_mom = o;
-    o += aa ? align_up((size_t)4 * (size_t)L.plane * (d->storage == LBM_F64 ? 8 : 4)) : 0;
+    L.off_edge = o;
+    const int max_strips = (d->nx + strip_cols(d->storage) - 1) / strip_cols(d->storage);
+    o += aa ? align_up((size_t)lbm::aa_edge_elems(d->nr, L.pitch, max_strips) * (d->storage == LBM_F64 ? 8 : 4)) : 0;
     const size_t nrd = align_up((size_t)d->nr * 8), nrf = align_up((size_t)d->nr * 4);
     L.off_uin_d = o; o += nrd;
     L.off_tin_d = o; o += nrd;
@@ -158,7 +159,6 @@ struct lbm_lattice {
     int device, sms;
     bool aa;               // AA pattern: one buffer (cur stays 0), moment planes
     int phase;             // AA pattern: representation of the stored state (lbm_aa.cuh)
-    int lag;               // AA pattern: lag of pass B in work items (0 = automatic)
 
     void *buf(int b) const { return mem + L.off_buf[b]; }
     template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(mem + off); }
@@ -227,7 +227,7 @@ lbm::StepParams<C> make_params(const lbm_lattice *h, const C *u_in, const C *T_i
     p.status = h->at<int>(h->L.off_status);
     p.aa = h->aa ? 1 : 0;
     p.phase = h->aa ? h->phase : 0;
-    p.mom = h->aa ? h->at<C>(h->L.off_mom) : nullptr;
+    p.edge = h->aa ? h->at<C>(h->L.off_edge) : nullptr;
     return p;
 }
 
@@ -277,55 +277,60 @@ int plan_launch(lbm_lattice *h)
     if (h->band > 0) {
         h->band_eff = h->band;
     } else {
-        const int64_t rounds10 = storage_bytes(h->d.storage) == 2 ? 34 : 45;  // tenths of a round
+        // tenths of a round (AA: 3.4 for every storage type; band 8 on the 4096 x 1024 jet,
+        // the fastest of bands 4..16 measured for FP32 and FP16)
+        const int64_t rounds10 = storage_bytes(h->d.storage) == 2 || h->aa ? 34 : 45;
         const int64_t want_tiles = std::max<int64_t>(1, rounds10 * resident_warps / 10);
         const int64_t band = ((int64_t)h->d.nr * nstrips + want_tiles - 1) / want_tiles;
         h->band_eff = (int)std::min<int64_t>(8, std::max<int64_t>(1, band));
     }
+    if (h->aa)  // the edge area holds the edge rows of bands of at least AA_BAND_MIN rows
+        h->band_eff = std::max(h->band_eff, std::min(lbm::AA_BAND_MIN, h->d.nr));
     const int64_t ntiles = (int64_t)nstrips * ((h->d.nr + h->band_eff - 1) / h->band_eff);
     h->ctas_max = per_sm * std::max(1, h->sms);
     h->ctas = (int)std::min<int64_t>(h->ctas_max, (ntiles + h->warps - 1) / h->warps);
     return LBM_OK;
 }
 
-// Schedule of an AA-pattern launch (lbm_aa.cuh): items per step, the lag
-// L of pass B behind pass A, and steps per launch.  With D the largest
-// item-index distance between neighbour items, every wait is on an earlier
-// job when D <= L <= items - 1 - D; lattices with items < 2 D + 1 run one
-// step per launch with L = items (all of pass A first).
+// Schedule of an AA-pattern launch (lbm_aa.cuh): an item waits in the
+// middle of its work for the edges of items up to D = one band of items
+// plus one further on, so at least D + 2 warps must be resident; items are
+// widened (more strips per item) until they are.
 struct AAPlan {
-    int64_t items, lag, per_launch;
-    bool multi;  // several steps per launch
+    int group;
+    int64_t items, per_launch;
+    int ctas;
 };
 
-AAPlan aa_plan(const lbm_lattice *h, int group)
+AAPlan aa_plan(const lbm_lattice *h)
 {
     const lbm_desc &d = h->d;
     const int nstrips = (d.nx + strip_cols(d.storage) - 1) / strip_cols(d.storage);
-    const int64_t cols = lbm::item_cols(nstrips, group);
+    const int64_t nbands = (d.nr + h->band_eff - 1) / h->band_eff;
+    const int64_t resident = (int64_t)h->ctas_max * h->warps;
     AAPlan a;
-    a.items = cols * ((d.nr + h->band_eff - 1) / h->band_eff);
-    const int64_t D = d.bc_in == LBM_IN_PERIODIC ? 2 * cols - 1 : cols + 1;
-    a.multi = a.items >= 2 * D + 1;
-    if (a.multi) {
-        const int64_t want = h->lag > 0 ? h->lag : D + (int64_t)h->ctas_max * h->warps / 2;
-        a.lag = std::min(std::max(want, D), a.items - 1 - D);
-        // jobs 2 (steps x items + lag) stay below 2^31
-        a.per_launch = std::max<int64_t>(1, (((int64_t)1 << 30) - 1 - a.lag) / a.items);
-    } else {
-        a.lag = a.items;
-        a.per_launch = 1;
+    for (a.group = std::max(1, item_group(h));; ++a.group) {
+        const int64_t cols = lbm::item_cols(nstrips, a.group);
+        a.items = cols * nbands;
+        const int64_t D = std::min<int64_t>(a.items - 1, cols + 1);
+        if (resident >= D + 2 || a.group >= nstrips)
+            break;
     }
+    const int64_t cols = lbm::item_cols(nstrips, a.group);
+    const int64_t D = std::min<int64_t>(a.items - 1, cols + 1);
+    a.ctas = (int)std::min<int64_t>(h->ctas_max, (std::max<int64_t>(a.items, D + 2) + h->warps - 1) / h->warps);
+    // the work counter stays below 2^31
+    a.per_launch = std::max<int64_t>(1, ((int64_t)1 << 31) / std::max<int64_t>(1, 2 * a.items));
     return a;
 }
 
-cudaError_t aa_launch(lbm_lattice *h, const lbm::RunCtl &ctl, int lag, int ctas, cudaStream_t s)
+cudaError_t aa_launch(lbm_lattice *h, const lbm::RunCtl &ctl, int ctas, cudaStream_t s)
 {
     switch (h->d.storage) {
-    case LBM_F64: return lbm::launch_aa_run_f64(params_d(h), ctl, lag, h->warps, ctas, s);
-    case LBM_F32: return lbm::launch_aa_run_f32(params_f(h), ctl, lag, h->warps, ctas, s);
-    case LBM_F16: return lbm::launch_aa_run_f16(params_f(h), ctl, lag, h->warps, ctas, s);
-    default: return lbm::launch_aa_run_bf16(params_f(h), ctl, lag, h->warps, ctas, s);
+    case LBM_F64: return lbm::launch_aa_run_f64(params_d(h), ctl, h->warps, ctas, s);
+    case LBM_F32: return lbm::launch_aa_run_f32(params_f(h), ctl, h->warps, ctas, s);
+    case LBM_F16: return lbm::launch_aa_run_f16(params_f(h), ctl, h->warps, ctas, s);
+    default: return lbm::launch_aa_run_bf16(params_f(h), ctl, h->warps, ctas, s);
     }
 }
 
@@ -613,7 +618,7 @@ int lattice_view(const lbm_lattice *h, LatticeView *out)
         return fail(LBM_ERR_INVALID_ARG, "bad handle or NULL output");
     out->storage = h->d.storage;
     out->device = h->device;
-    out->prev_valid = h->prev_valid ? 1 : 0;
+    out->prev_valid = h->prev_valid && !h->aa ? 1 : 0;
     out->nx = h->d.nx;
     out->nr = h->d.nr;
     if (h->d.storage == LBM_F64)
@@ -672,7 +677,6 @@ int lbm_create(const lbm_desc *d, void *dev_mem, size_t bytes, lbm_lattice **out
     h->group = 0;
     h->aa = d->pattern == LBM_PATTERN_AA;
     h->phase = 0;
-    h->lag = 0;
     cudaGetDevice(&h->device);
     h->sms = 1;
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -798,21 +802,21 @@ int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
     lbm::RunCtl ctl;
     ctl.group = item_group(h);
     if (h->aa) {
-        const AAPlan a = aa_plan(h, ctl.group);
+        const AAPlan a = aa_plan(h);
         unsigned *sync = h->at<unsigned>(h->L.off_sync);
+        ctl.group = a.group;
         ctl.counter = sync;
         ctl.flags = sync + 1;
         ctl.radius = 1;
         ctl.wrap = d.bc_in == LBM_IN_PERIODIC ? 1 : 0;
         ctl.spin_limit = lbm::RUN_SPIN_LIMIT;
-        const int ctas = (int)std::min<int64_t>(h->ctas_max, (a.items + h->warps - 1) / h->warps);
         for (int64_t done = 0; done < nsteps;) {
             const int m = (int)std::min<int64_t>(a.per_launch, nsteps - done);
             cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)4 * (size_t)(1 + 2 * a.items), s);
             if (e != cudaSuccess)
                 return cuda_fail(e, "work counter reset");
             ctl.nsteps = m;
-            e = aa_launch(h, ctl, (int)a.lag, ctas, s);
+            e = aa_launch(h, ctl, a.ctas, s);
             if (e != cudaSuccess)
                 return cuda_fail(e, "step kernel launch");
             h->phase ^= (m & 1);
@@ -878,16 +882,17 @@ int lbm_selftest_wait_timeout(lbm_lattice *h, int32_t *flags)
     ctl.spin_limit = 64;  // a few tens of microseconds
     ctl.nsteps = 2;
     if (h->aa) {
-        // every counter at zero and the work counter past every job of
-        // sub-step 0: each job taken belongs to sub-step 1 and waits
-        const AAPlan a = aa_plan(h, ctl.group);
+        // every counter at zero and the work counter past sub-step 0: each
+        // item taken belongs to sub-step 1 and waits for a sub-step that never runs
+        const AAPlan a = aa_plan(h);
+        ctl.group = a.group;
         ctl.radius = 1;
-        const unsigned start = (unsigned)(2 * (a.items + a.lag));
+        const unsigned start = (unsigned)a.items;
         cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)4 * (size_t)(1 + 2 * a.items), s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(sync, &start, sizeof(unsigned), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess)
-            e = aa_launch(h, ctl, (int)a.lag, (int)std::min<int64_t>(h->ctas_max, (a.items + h->warps - 1) / h->warps), s);
+            e = aa_launch(h, ctl, a.ctas, s);
         if (e != cudaSuccess)
             return cuda_fail(e, "self-test launch");
         return lbm_check(h, flags);
@@ -921,22 +926,6 @@ int lbm_set_item_group(lbm_lattice *h, int32_t group)
 
 int32_t lbm_get_item_group(const lbm_lattice *h) { return valid(h) ? item_group(h) : -1; }
 
-int lbm_set_aa_lag(lbm_lattice *h, int32_t lag)
-{
-    if (!valid(h) || !h->aa || lag < 0)
-        return fail(LBM_ERR_INVALID_ARG, "bad handle, not an AA-pattern lattice, or negative lag");
-    h->lag = lag;
-    return LBM_OK;
-}
-
-int32_t lbm_get_aa_lag(const lbm_lattice *h)
-{
-    if (!valid(h) || !h->aa)
-        return -1;
-    const AAPlan a = aa_plan(h, item_group(h));
-    return a.multi ? (int32_t)a.lag : 0;
-}
-
 int64_t lbm_get_step(const lbm_lattice *h) { return valid(h) ? h->step : -1; }
 
 int lbm_diagnostics(lbm_lattice *h, lbm_diag *out, lbm_stream stream)
@@ -949,7 +938,7 @@ int lbm_diagnostics(lbm_lattice *h, lbm_diag *out, lbm_stream stream)
         {(int64_t)lbm::DIAG_MAX_BLOCKS, (N + lbm::DIAG_THREADS - 1) / lbm::DIAG_THREADS, 4 * (int64_t)h->sms});
     double *partials = h->at<double>(h->L.off_diag);
     double *res = partials + (size_t)lbm::DIAG_MAX_BLOCKS * lbm::DIAG_SLOTS;
-    const int prev = h->prev_valid ? 1 : 0;
+    const int prev = h->prev_valid && !h->aa ? 1 : 0;  // an AA lattice keeps no previous state
     cudaError_t e;
     switch (h->d.storage) {
     case LBM_F64: e = lbm::launch_diag_f64(params_d(h), prev, partials, nblocks, res, s); break;

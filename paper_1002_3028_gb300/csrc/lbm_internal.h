@@ -28,8 +28,8 @@ namespace lbm {
                                       int pitch, int64_t plane, double rho0, double T0, cudaStream_t s); \
     cudaError_t launch_state_out_##TAG(const void *buf, double *f, double *g, int nx, int nr, int pitch, \
                                        int64_t plane, double rho0, double T0, cudaStream_t s);            \
-    cudaError_t launch_aa_run_##TAG(const StepParams<C> &p, const RunCtl &ctl, int lag, int warps_per_cta, \
-                                    int ctas, cudaStream_t s);                                          \
+    cudaError_t launch_aa_run_##TAG(const StepParams<C> &p, const RunCtl &ctl, int warps_per_cta, int ctas, \
+                                    cudaStream_t s);                                                    \
     cudaError_t occupancy_aa_run_##TAG(int warps_per_cta, int *ctas_per_sm);                           \
     cudaError_t launch_aa_fill_##TAG(const StepParams<C> &p, cudaStream_t s);                          \
     cudaError_t launch_aa_state_in_##TAG(void *buf, const double *f, const double *g, int nx, int nr,  \

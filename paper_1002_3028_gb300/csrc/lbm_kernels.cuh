@@ -96,7 +96,7 @@ struct alignas(16) StepParams {
     const C *u_in, *T_in;         // inlet profiles, nr values
     const C *nu_tab, *al_tab;     // property tables, ntab values
     int *status;                  // error flags of the lattice
-    C *mom;                       // AA layout: 4 planes of the last step's moments (see lbm_aa.cuh)
+    C *edge;                      // AA layout: moments at the warp tiles' edges (see lbm_aa.cuh)
     int aa;                       // 1: one buffer in the AA layout (src == dst); 0: two buffers
     int phase;                    // AA layout: representation of the stored state
 };
@@ -442,21 +442,12 @@ __device__ __forceinline__ Mom<V> ghost_top(const StepParams<C> &p, Mom<V> m)
 }
 
 // Eq. 2 moments at node (i, j) (deviations from rest) of the populations
-// streamed from the stored state, or (previous) of the step before: from
-// the other buffer (two-buffer layout) or the stored moment planes (AA)
+// streamed from the stored state, or (previous, two-buffer layout only) of
+// those streamed from the other buffer, the state one step earlier
 template <class S, class C>
 __device__ __forceinline__ Mom<Vec<C, 1>> node_moments(const StepParams<C> &p, int i, int j, bool previous)
 {
     using V1 = Vec<C, 1>;
-    if (previous && p.aa) {
-        const int64_t o = cell(p, 0, i, j);
-        Mom<V1> m;
-        m.drho = V1(__ldcg(p.mom + o));
-        m.jx = V1(__ldcg(p.mom + p.plane + o));
-        m.jr = V1(__ldcg(p.mom + 2 * p.plane + o));
-        m.dT = V1(__ldcg(p.mom + 3 * p.plane + o));
-        return m;
-    }
     C f[9], g[4];
     pull<S, C>(p, static_cast<const S *>(previous ? p.dst : p.src), i, j, f, g);
     V1 vf[9], vg[4];
@@ -1179,8 +1170,8 @@ __global__ void fields_kernel(const __grid_constant__ StepParams<C> p, O *out)
 }
 
 // ---- FP64 diagnostics: mass, heat, steady residual, divergence -------------------------
-// Per node, from the populations streamed from the current state (and the
-// moments of the previous step): rho, u, T of Eq. 2.  Sums run in
+// Per node, from the populations streamed from the current state (and from
+// the previous state in the other buffer): rho, u, T of Eq. 2.  Sums run in
 // FP64: Σ rho, Σ r rho, Σ T, Σ r T, Σ |u(t) - u(t-1)|^2, Σ |u(t)|^2,
 // max |u(t) - u(t-1)|, max |u(t)|, and the count of nodes whose rho is not
 // finite and positive or whose T is not finite.  Block partials go to

@@ -45,7 +45,7 @@ int scratch_on(int device, double **ptr)
 }
 
 // One CTA per lattice row: the row's nodes (populations streamed from the
-// current state, moments of the previous step) reduced in FP64 into the
+// current state, and from the previous one in the other buffer) reduced in FP64 into the
 // row's DIAG_SLOTS partial slots; same per-node quantities as the
 // lattice-scratch diagnostics.
 template <class S, class C>

@@ -110,13 +110,13 @@ cudaError_t LBM_CAT(launch_state_out_, LBM_TAG)(const void *buf, double *f, doub
 }
 
 // ---- AA layout ------------------------------------------------------------------------
-cudaError_t LBM_CAT(launch_aa_run_, LBM_TAG)(const StepParams<LBM_C> &p, const RunCtl &ctl, int lag, int warps_per_cta,
-                                             int ctas, cudaStream_t s)
+cudaError_t LBM_CAT(launch_aa_run_, LBM_TAG)(const StepParams<LBM_C> &p, const RunCtl &ctl, int warps_per_cta, int ctas,
+                                             cudaStream_t s)
 {
     if (p.ntiles <= 0 || ctl.nsteps <= 0)
         return cudaSuccess;
     const int smem = run_smem<LBM_S, LBM_C>(warps_per_cta);
-    aa_run_kernel<LBM_S, LBM_C><<<ctas, 32 * warps_per_cta, smem, s>>>(p, ctl, lag);
+    aa_run_kernel<LBM_S, LBM_C><<<ctas, 32 * warps_per_cta, smem, s>>>(p, ctl);
     return cudaGetLastError();
 }
 

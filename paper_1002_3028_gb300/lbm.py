@@ -113,9 +113,6 @@ def lib(build: bool = True):
             L.lbm_selftest_wait_timeout.argtypes = [vp, C.POINTER(i32)]
             L.lbm_get_item_group.restype = i32
             L.lbm_get_item_group.argtypes = [vp]
-            L.lbm_set_aa_lag.argtypes = [vp, i32]
-            L.lbm_get_aa_lag.restype = i32
-            L.lbm_get_aa_lag.argtypes = [vp]
             L.lbm_check.argtypes = [vp, C.POINTER(i32)]
             L.lbm_diagnostics.argtypes = [vp, C.POINTER(Diag), vp]
             L.lbm_diagnostics_noalloc.argtypes = [vp, C.POINTER(Diag), vp]
@@ -133,7 +130,7 @@ def lib(build: bool = True):
                          "lbm_step", "lbm_get_fields", "lbm_get_state", "lbm_set_state",
                          "lbm_set_launch", "lbm_get_launch", "lbm_check", "lbm_batch_create",
                          "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_set_launch",
-                         "lbm_batch_get_launch", "lbm_diagnostics", "lbm_diagnostics_noalloc", "lbm_set_aa_lag"):
+                         "lbm_batch_get_launch", "lbm_diagnostics", "lbm_diagnostics_noalloc"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -166,7 +163,8 @@ class Lattice:
     """One lattice resident on the GPU, advanced by the fused CUDA step.
 
     ``pattern`` is the memory layout: "ab" (two population buffers) or "aa"
-    (one buffer updated in place, plus the moment planes; same results).
+    (one buffer updated in place, plus the tiles' edge moments; same results,
+    no steady residual).
     """
 
     def __init__(self, cfg: LatticeConfig, storage: str = "f32", device=None, pattern: str = "ab"):
@@ -245,15 +243,6 @@ class Lattice:
     @property
     def item_group(self) -> int:
         return int(self._L.lbm_get_item_group(self._h))
-
-    def set_aa_lag(self, lag: int = 0):
-        """AA pattern: lag of the collision pass in work items (0 = automatic)."""
-        _check(self._L.lbm_set_aa_lag(self._h, int(lag)), "lbm_set_aa_lag")
-
-    @property
-    def aa_lag(self) -> int:
-        """Lag lbm_step uses (0: one step per launch; -1: not an AA lattice)."""
-        return int(self._L.lbm_get_aa_lag(self._h))
 
     def launch(self):
         """(band rows, warps per CTA, CTAs) used by lbm_step."""
