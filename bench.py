@@ -329,8 +329,6 @@ def run_gpu(args):
 
     works = workloads_by_name(args.workload)
     label = workload_label(args.workload, works)
-    if args.pattern == "aa" and len(works) > 1:
-        raise SystemExit("the AA pattern steps single lattices, not batches")
     lats = [lbm.Lattice.from_workload(w, args.storage, device=device, pattern=args.pattern) for w in works]
     nodes = sum(w.nodes for w in works)
     stream = torch.cuda.current_stream(device)
@@ -464,7 +462,8 @@ def run_serving(args):
     reqs = I.request_stream(count=args.requests, rate_per_s=args.rate, seed=11)
     torch.cuda.synchronize()
     with ClockSampler(0) as clk:
-        batched = serve(reqs, GpuBatchEngine("f16"), args.budget_gb * 1e9, chunk=args.chunk, keep_fields=True)
+        batched = serve(reqs, GpuBatchEngine("f16", pattern=args.pattern), args.budget_gb * 1e9, chunk=args.chunk,
+                        keep_fields=True)
     torch.cuda.synchronize()
     plain = serve_plain(reqs, "f32")
     # error of the served FP16 fields against an FP64 run of the same request, on a sample
@@ -486,7 +485,7 @@ def run_serving(args):
         "data": "synthetic",
         "config": {"workload": f"serving: {len(reqs)} Poisson requests at {args.rate}/s, jets drawn like the "
                                f"ensemble, steps U{{1000..20000}}, seed 11", "storage": "f16 (batched), f32 (plain)",
-                   "budget_gb": args.budget_gb, "chunk_steps": args.chunk},
+                   "pattern": args.pattern + " (batched)", "budget_gb": args.budget_gb, "chunk_steps": args.chunk},
         "serving": {"batched_f16": b, "plain_f32_one_at_a_time": p_,
                     "mlups_ratio_batched_over_plain": b["mlups"] / p_["mlups"],
                     "f16_error_vs_f64_sample": errs},

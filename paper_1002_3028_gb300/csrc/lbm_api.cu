@@ -173,8 +173,10 @@ struct lbm_batch {
     size_t cap_params;
     lbm::TileRef *d_tiles;
     size_t cap_tiles;
-    unsigned *d_sync;  // multi-step launch: work counter, then one counter per table entry (cap_tiles + 1)
+    unsigned *d_sync;  // multi-step launch: work counter, then one or (AA) two counters per table entry
     int ntiles;
+    bool aa;           // members use the AA pattern (all members share one pattern)
+    int aa_ctas_min;   // AA: CTAs that cover the widest member's edge-wait distance
     int band, warps, band_eff;
     int sms;
     int ctas_max;  // CTAs resident on the device at once (persistent grid)
@@ -413,10 +415,10 @@ int batch_occupancy(lbm_batch *b, int warps, int *per_sm)
 {
     cudaError_t e;
     switch (b->storage) {
-    case LBM_F64: e = lbm::occupancy_batch_f64(warps, per_sm); break;
-    case LBM_F32: e = lbm::occupancy_batch_f32(warps, per_sm); break;
-    case LBM_F16: e = lbm::occupancy_batch_f16(warps, per_sm); break;
-    default: e = lbm::occupancy_batch_bf16(warps, per_sm); break;
+    case LBM_F64: e = b->aa ? lbm::occupancy_aa_batch_f64(warps, per_sm) : lbm::occupancy_batch_f64(warps, per_sm); break;
+    case LBM_F32: e = b->aa ? lbm::occupancy_aa_batch_f32(warps, per_sm) : lbm::occupancy_batch_f32(warps, per_sm); break;
+    case LBM_F16: e = b->aa ? lbm::occupancy_aa_batch_f16(warps, per_sm) : lbm::occupancy_batch_f16(warps, per_sm); break;
+    default: e = b->aa ? lbm::occupancy_aa_batch_bf16(warps, per_sm) : lbm::occupancy_batch_bf16(warps, per_sm); break;
     }
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "batch occupancy query");
 }
@@ -433,6 +435,7 @@ void drop_graph(lbm_batch *b)
 int batch_rebuild(lbm_batch *b, cudaStream_t s)
 {
     const int n = (int)b->members.size();
+    b->aa = n > 0 && b->members[0]->aa;
     int per_sm = 0;
     int rc = batch_occupancy(b, b->warps, &per_sm);
     if (rc)
@@ -453,6 +456,17 @@ int batch_rebuild(lbm_batch *b, cudaStream_t s)
         const int64_t band = (area + want_tiles - 1) / want_tiles;
         b->band_eff = (int)std::min<int64_t>(16, std::max<int64_t>(1, band));
     }
+    if (b->aa)  // the members' edge areas hold bands of at least AA_BAND_MIN rows
+        b->band_eff = std::max(b->band_eff, lbm::AA_BAND_MIN);
+    // AA: an item waits on the edges of items up to one band of its lattice's tiles plus one
+    // away, so the launch needs that many warps plus two for the widest member
+    int max_strips = 1;
+    for (lbm_lattice *h : b->members)
+        max_strips = std::max(max_strips, (h->d.nx + cols - 1) / cols);
+    b->aa_ctas_min = (max_strips + 3 + b->warps - 1) / b->warps;
+    if (b->aa && b->aa_ctas_min > per_sm * std::max(1, b->sms))
+        return fail(LBM_ERR_INVALID_ARG, "an AA batch member of %d strips is too wide for the resident warps",
+                    max_strips);
     std::vector<lbm::TileRef> tiles;
     std::vector<unsigned char> params(params_size(b->storage) * (size_t)std::max(1, n));
     for (int m = 0; m < n; ++m) {
@@ -492,7 +506,7 @@ int batch_rebuild(lbm_batch *b, cudaStream_t s)
             const size_t cap = std::max<size_t>(1, tiles.size() * 2);
             e = cudaMalloc(&b->d_tiles, cap * sizeof(lbm::TileRef));
             if (e == cudaSuccess)
-                e = cudaMalloc(&b->d_sync, (cap + 1) * sizeof(unsigned));
+                e = cudaMalloc(&b->d_sync, (2 * cap + 1) * sizeof(unsigned));
             b->cap_tiles = e == cudaSuccess ? cap : 0;
         }
         if (e != cudaSuccess) {
@@ -517,7 +531,7 @@ int batch_rebuild(lbm_batch *b, cudaStream_t s)
 cudaError_t batch_launch(lbm_batch *b, int nsteps, cudaStream_t s)
 {
     const int n = (int)b->members.size();
-    cudaError_t e = cudaMemsetAsync(b->d_sync, 0, (size_t)(b->ntiles + 1) * sizeof(unsigned), s);
+    cudaError_t e = cudaMemsetAsync(b->d_sync, 0, (size_t)((b->aa ? 2 : 1) * b->ntiles + 1) * sizeof(unsigned), s);
     if (e != cudaSuccess)
         return e;
     lbm::RunCtl ctl;
@@ -528,7 +542,25 @@ cudaError_t batch_launch(lbm_batch *b, int nsteps, cudaStream_t s)
     ctl.wrap = 0;  // read from each lattice's parameters
     ctl.spin_limit = lbm::RUN_SPIN_LIMIT;
     ctl.group = 1;
-    const int ctas = (int)std::min<int64_t>(b->ctas_max, ((int64_t)b->ntiles + b->warps - 1) / b->warps);
+    int ctas = (int)std::min<int64_t>(b->ctas_max, ((int64_t)b->ntiles + b->warps - 1) / b->warps);
+    if (b->aa) {
+        ctas = std::min(b->ctas_max, std::max(ctas, b->aa_ctas_min));
+        ctl.radius = 1;
+        switch (b->storage) {
+        case LBM_F64:
+            return lbm::launch_aa_batch_f64(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<double> *>(b->d_params),
+                                            n, ctl, b->warps, ctas, s);
+        case LBM_F32:
+            return lbm::launch_aa_batch_f32(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params),
+                                            n, ctl, b->warps, ctas, s);
+        case LBM_F16:
+            return lbm::launch_aa_batch_f16(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params),
+                                            n, ctl, b->warps, ctas, s);
+        default:
+            return lbm::launch_aa_batch_bf16(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params),
+                                             n, ctl, b->warps, ctas, s);
+        }
+    }
     switch (b->storage) {
     case LBM_F64:
         return lbm::launch_batch_f64(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<double> *>(b->d_params), n,
@@ -583,7 +615,9 @@ void batch_advance_host(lbm_batch *b, int nsteps)
 {
     for (lbm_lattice *h : b->members) {
         h->step += nsteps;
-        if (nsteps & 1)
+        if (h->aa)
+            h->phase ^= nsteps & 1;
+        else if (nsteps & 1)
             h->cur = 1 - h->cur;
         if (nsteps > 0)
             h->prev_valid = true;
@@ -1173,8 +1207,8 @@ int lbm_batch_add(lbm_batch *b, lbm_lattice *h)
         return fail(LBM_ERR_INVALID_ARG, "the lattice already belongs to a batch");
     if (h->d.storage != b->storage)
         return fail(LBM_ERR_INVALID_ARG, "storage type %d differs from the batch's %d", h->d.storage, b->storage);
-    if (h->aa)
-        return fail(LBM_ERR_INVALID_ARG, "AA-pattern lattices are stepped alone, not in batches");
+    if (!b->members.empty() && b->members[0]->aa != h->aa)
+        return fail(LBM_ERR_INVALID_ARG, "the members of a batch share one pattern");
     b->members.push_back(h);
     h->batch = b;
     b->dirty = true;

@@ -6,7 +6,7 @@
 #include <stdint.h>
 
 #include "lbm.h"
-#include "lbm_aa.cuh"
+#include "lbm_aa_batch.cuh"
 
 namespace lbm {
 
@@ -31,6 +31,9 @@ namespace lbm {
     cudaError_t launch_aa_run_##TAG(const StepParams<C> &p, const RunCtl &ctl, int warps_per_cta, int ctas, \
                                     cudaStream_t s);                                                    \
     cudaError_t occupancy_aa_run_##TAG(int warps_per_cta, int *ctas_per_sm);                           \
+    cudaError_t launch_aa_batch_##TAG(const TileRef *tiles, int ntiles, StepParams<C> *lattices, int nlat,  \
+                                      const RunCtl &ctl, int warps_per_cta, int ctas, cudaStream_t s); \
+    cudaError_t occupancy_aa_batch_##TAG(int warps_per_cta, int *ctas_per_sm);                         \
     cudaError_t launch_aa_fill_##TAG(const StepParams<C> &p, cudaStream_t s);                          \
     cudaError_t launch_aa_state_in_##TAG(void *buf, const double *f, const double *g, int nx, int nr,  \
                                          int pitch, int64_t plane, double rho0, double T0, cudaStream_t s); \

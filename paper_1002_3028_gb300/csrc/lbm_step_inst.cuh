@@ -130,6 +130,33 @@ cudaError_t LBM_CAT(occupancy_aa_run_, LBM_TAG)(int warps_per_cta, int *ctas_per
                                                          run_smem<LBM_S, LBM_C>(warps_per_cta));
 }
 
+cudaError_t LBM_CAT(launch_aa_batch_, LBM_TAG)(const TileRef *tiles, int ntiles, StepParams<LBM_C> *lattices,
+                                               int nlat, const RunCtl &ctl, int warps_per_cta, int ctas,
+                                               cudaStream_t s)
+{
+    if (ntiles <= 0 || nlat <= 0 || ctl.nsteps <= 0)
+        return cudaSuccess;
+    const int smem = warps_per_cta * batch_smem_per_warp<LBM_S, LBM_C>();
+    aa_batch_run_kernel<LBM_S, LBM_C><<<ctas, 32 * warps_per_cta, smem, s>>>(tiles, ntiles, lattices, ctl);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    aa_advance_kernel<LBM_C><<<(nlat + 127) / 128, 128, 0, s>>>(lattices, nlat, ctl.nsteps);
+    return cudaGetLastError();
+}
+
+cudaError_t LBM_CAT(occupancy_aa_batch_, LBM_TAG)(int warps_per_cta, int *ctas_per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute(aa_batch_run_kernel<LBM_S, LBM_C>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         8 * batch_smem_per_warp<LBM_S, LBM_C>());
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, aa_batch_run_kernel<LBM_S, LBM_C>,
+                                                         32 * warps_per_cta,
+                                                         warps_per_cta * batch_smem_per_warp<LBM_S, LBM_C>());
+}
+
 cudaError_t LBM_CAT(launch_aa_fill_, LBM_TAG)(const StepParams<LBM_C> &p, cudaStream_t s)
 {
     const int64_t N = (int64_t)p.nx * p.nr;

@@ -136,15 +136,20 @@ def serve(requests: List[Request], engine: Engine, budget_bytes: float, chunk: i
 
 
 class GpuBatchEngine(Engine):
-    """All active lattices in one liblbm batch (persistent multi-step launches, graph replay)."""
+    """All active lattices in one liblbm batch (persistent multi-step launches, graph replay).
 
-    def __init__(self, storage: str = "f16", device=None, graph: bool = True):
+    ``pattern="aa"`` keeps every lattice in one population buffer updated in place, so the
+    same memory budget admits more lattices (FP16: about 32 instead of 52 bytes per node).
+    """
+
+    def __init__(self, storage: str = "f16", device=None, graph: bool = True, pattern: str = "ab"):
         import torch
 
         from . import lbm
 
         self.lbm = lbm
         self.storage = storage
+        self.pattern = pattern
         self.device = torch.device(device if device is not None else "cuda")
         self.batch = lbm.Batch(storage)
         self.graph = graph
@@ -152,10 +157,10 @@ class GpuBatchEngine(Engine):
 
     def bytes_needed(self, req: Request) -> int:
         w = req.workload
-        return self.lbm.required_bytes(w.cfg, self.storage) + 4 * 4 * w.nodes
+        return self.lbm.required_bytes(w.cfg, self.storage, self.pattern) + 4 * 4 * w.nodes
 
     def admit(self, req: Request):
-        lat = self.lbm.Lattice.from_workload(req.workload, self.storage, device=self.device)
+        lat = self.lbm.Lattice.from_workload(req.workload, self.storage, device=self.device, pattern=self.pattern)
         self.batch.add(lat)
         return lat
 

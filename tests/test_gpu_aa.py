@@ -232,9 +232,11 @@ def test_aa_memory_and_batches(lbm):
     assert per_node["f16"][0] == pytest.approx(52, rel=0.05) and per_node["f16"][1] == pytest.approx(32, rel=0.05)
     assert per_node["f64"][1] == pytest.approx(116, rel=0.05)
     aa = lbm.Lattice(I.LatticeConfig(nx=64, nr=16), "f16", pattern="aa")
+    ab = lbm.Lattice(I.LatticeConfig(nx=64, nr=16), "f16")
     batch = lbm.Batch("f16")
-    with pytest.raises(lbm.LbmError):
-        batch.add(aa)
+    batch.add(aa)
+    with pytest.raises(lbm.LbmError):  # the members of a batch share one pattern
+        batch.add(ab)
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
@@ -248,3 +250,45 @@ def test_aa_full_size_4096x1024(lbm, orc, storage):
     assert torch.equal(ab.save()[0], aa.save()[0])
     assert torch.equal(ab.fields(), aa.fields())
     assert aa.check() == 0
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "f64"])
+def test_aa_batch_members_equal_two_buffer_lattices_alone(lbm, orc, storage):
+    """A batch of ragged AA lattices (every boundary set, one of them a single tile)
+    advances every member exactly as a two-buffer lattice stepped alone: through graph
+    replays of 64 steps and a remainder launch, and after members leave and join."""
+    sizes = [(150, 45), (64, 16), (33, 5), (200, 70), (97, 40), (40, 9), (300, 61)]
+    names = sorted(BOUNDARIES)
+    pairs = []
+    batch = lbm.Batch(storage)
+    for m, ((nx, nr), bname) in enumerate(zip(sizes, names)):
+        ab, aa = twins(lbm, orc, workload(nx, nr, **BOUNDARIES[bname]), storage, seed=40 + m)
+        pairs.append((ab, aa))
+        batch.add(aa)
+    for n in (1, 64 + 37):
+        batch.step(n, graph=True)
+        for ab, _ in pairs:
+            ab.step(n)
+        for ab, aa in pairs:
+            assert_same(ab, aa)
+    batch.remove(pairs[2][1])
+    pairs[2][0].close()
+    batch.step(7, graph=False)
+    for k, (ab, aa) in enumerate(pairs):
+        if k != 2:
+            ab.step(7)
+            assert_same(ab, aa)
+        assert aa.check() == 0
+
+
+def test_aa_serving_engine_admits_by_aa_size(lbm):
+    """The serving engine with AA lattices counts their smaller footprint for admission."""
+    from paper_1002_3028_gb300.serve import GpuBatchEngine
+
+    w = I.ensemble_workloads(1, seed=7)[0]
+    req = I.Request(0, 0.0, w)
+    ab, aa = GpuBatchEngine("f16"), GpuBatchEngine("f16", pattern="aa")
+    assert aa.bytes_needed(req) < 0.75 * ab.bytes_needed(req)
+    lat = aa.admit(req)
+    aa.step(10)
+    assert lat.step_count == 10 and lat.check() == 0
