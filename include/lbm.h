@@ -87,8 +87,8 @@ typedef enum { LBM_BOTTOM_AXIS = 0, LBM_BOTTOM_WALL = 1 } lbm_bc_bottom;
  *                   instead of 52; FP64 about 116 instead of 208).  Results
  *                   are bit for bit those of LBM_PATTERN_AB, except that
  *                   no previous state is kept (lbm_diagnostics reports no
- *                   residual).  Bands are at least 4 rows.  Not for batch
- *                   members. */
+ *                   residual).  Bands are at least 4 rows.  Batches hold
+ *                   lattices of one pattern. */
 typedef enum { LBM_PATTERN_AB = 0, LBM_PATTERN_AA = 1 } lbm_pattern;
 
 /*
@@ -318,7 +318,7 @@ LBM_API int32_t lbm_get_item_group(const lbm_lattice *h);
  *                      change the membership (takes effect at the next
  *                      lbm_batch_step; a lattice belongs to one batch at a
  *                      time; lbm_step on a member is an error; lbm_destroy
- *                      removes it; LBM_PATTERN_AA lattices are refused).  Members keep their own state, inlet,
+ *                      removes it; all members share one lbm_pattern).  Members keep their own state, inlet,
  *                      tables and step counter; lbm_get_fields and friends
  *                      work on members as usual.
  *   lbm_batch_step     nsteps steps of every member on the stream; with
