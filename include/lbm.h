@@ -318,9 +318,10 @@ LBM_API int32_t lbm_get_item_group(const lbm_lattice *h);
  *                      change the membership (takes effect at the next
  *                      lbm_batch_step; a lattice belongs to one batch at a
  *                      time; lbm_step on a member is an error; lbm_destroy
- *                      removes it; all members share one lbm_pattern).  Members keep their own state, inlet,
- *                      tables and step counter; lbm_get_fields and friends
- *                      work on members as usual.
+ *                      removes it; all members share one lbm_pattern).
+ *                      Members keep their own state, inlet, tables and
+ *                      step counter; lbm_get_fields and friends work on
+ *                      members as usual.
  *   lbm_batch_step     nsteps steps of every member on the stream; with
  *                      use_graph != 0, whole chunks of 64 steps are replayed
  *                      from a captured CUDA graph of one launch (re-captured
