@@ -1,6 +1,7 @@
 // C ABI of liblbm (declared in include/lbm.h): lattice handles, device
-// memory layout, table uploads, the persistent multi-step launches of one
-// lattice and of batches, state I/O, checkpoints and diagnostics.
+// memory layout (two population buffers, or one in the AA pattern), table
+// uploads, the persistent multi-step launches of one lattice and of
+// batches, state I/O, checkpoints and diagnostics.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -157,7 +158,7 @@ struct lbm_lattice {
     int ctas_max;          // CTAs resident on the device at once (persistent grid)
     int group;             // warp tiles per work item of lbm_step (0 = automatic)
     int device, sms;
-    bool aa;               // AA pattern: one buffer (cur stays 0), moment planes
+    bool aa;               // AA pattern: one buffer (cur stays 0) and the tiles' edge moments
     int phase;             // AA pattern: representation of the stored state (lbm_aa.cuh)
 
     void *buf(int b) const { return mem + L.off_buf[b]; }

@@ -36,6 +36,9 @@
 // (step_run_kernel; batches: batch_run_kernel): warps take warp tiles in
 // step-major order, and a tile of step t + 1 starts once the tiles around it
 // have finished step t (see "many steps of one lattice in one launch").
+// Lattices kept in one buffer updated in place use the kernels of
+// lbm_aa.cuh and lbm_aa_batch.cuh, built from the same staging, moment,
+// collision and boundary code.
 #pragma once
 
 #include <cuda_bf16.h>
