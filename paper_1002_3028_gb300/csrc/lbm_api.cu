@@ -177,6 +177,7 @@ struct lbm_batch {
     unsigned *d_sync;  // multi-step launch: work counter, then one or (AA) two counters per table entry
     int ntiles;
     bool aa;           // members use the AA pattern (all members share one pattern)
+    bool far;          // a periodic member has a one-column last strip (lbm::far_wrap)
     int aa_ctas_min;   // AA: CTAs that cover the widest member's edge-wait distance
     int band, warps, band_eff;
     int sms;
@@ -462,8 +463,12 @@ int batch_rebuild(lbm_batch *b, cudaStream_t s)
     // AA: an item waits on the edges of items up to one band of its lattice's tiles plus one
     // away, so the launch needs that many warps plus two for the widest member
     int max_strips = 1;
-    for (lbm_lattice *h : b->members)
-        max_strips = std::max(max_strips, (h->d.nx + cols - 1) / cols);
+    b->far = false;
+    for (lbm_lattice *h : b->members) {
+        const int ns = (h->d.nx + cols - 1) / cols;
+        max_strips = std::max(max_strips, ns);
+        b->far = b->far || lbm::far_wrap(h->d.bc_in, h->d.nx, ns, cols);
+    }
     b->aa_ctas_min = (max_strips + 3 + b->warps - 1) / b->warps;
     if (b->aa && b->aa_ctas_min > per_sm * std::max(1, b->sms))
         return fail(LBM_ERR_INVALID_ARG, "an AA batch member of %d strips is too wide for the resident warps",
@@ -565,16 +570,16 @@ cudaError_t batch_launch(lbm_batch *b, int nsteps, cudaStream_t s)
     switch (b->storage) {
     case LBM_F64:
         return lbm::launch_batch_f64(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<double> *>(b->d_params), n,
-                                     ctl, b->warps, ctas, s);
+                                     ctl, b->warps, ctas, b->far ? 1 : 0, s);
     case LBM_F32:
         return lbm::launch_batch_f32(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params), n,
-                                     ctl, b->warps, ctas, s);
+                                     ctl, b->warps, ctas, b->far ? 1 : 0, s);
     case LBM_F16:
         return lbm::launch_batch_f16(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params), n,
-                                     ctl, b->warps, ctas, s);
+                                     ctl, b->warps, ctas, b->far ? 1 : 0, s);
     default:
         return lbm::launch_batch_bf16(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params), n,
-                                      ctl, b->warps, ctas, s);
+                                      ctl, b->warps, ctas, b->far ? 1 : 0, s);
     }
 }
 

@@ -18,7 +18,7 @@ namespace lbm {
                                  cudaStream_t s);                                                      \
     cudaError_t occupancy_run_##TAG(int warps_per_cta, int *ctas_per_sm);                              \
     cudaError_t launch_batch_##TAG(const TileRef *tiles, int ntiles, StepParams<C> *lattices, int nlat,     \
-                                   const RunCtl &ctl, int warps_per_cta, int ctas, cudaStream_t s);    \
+                                   const RunCtl &ctl, int warps_per_cta, int ctas, int far, cudaStream_t s); \
     cudaError_t occupancy_batch_##TAG(int warps_per_cta, int *ctas_per_sm);                            \
     cudaError_t launch_fields_##TAG(const StepParams<C> &p, void *out, int out_f64, cudaStream_t s);   \
     cudaError_t launch_fill_##TAG(const StepParams<C> &p, cudaStream_t s);                             \

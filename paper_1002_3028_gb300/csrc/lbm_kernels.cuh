@@ -980,13 +980,16 @@ __device__ __forceinline__ void red_release_add(unsigned *a, unsigned v)
 
 // Every lane waits until the items around item (band b, column g) of a
 // lattice (its counters start at `flags`, `cols` items per band) have
-// finished sub-step k - 1.  Returns false if the wait runs out or another
-// warp's wait ran out (the status word is read only while waiting).
+// finished sub-step k - 1: radius bands and one item column on each side,
+// and also the items two columns out when `far`.  Returns false if the
+// wait runs out or another warp's wait ran out (the status word is read
+// only while waiting).
 template <class C>
 __device__ bool wait_neighbours(const StepParams<C> &p, const unsigned *flags, int cols, int radius, bool wrap, int b,
-                                int g, int k, int spin_limit)
+                                int g, int k, int spin_limit, bool far = false)
 {
-    // lane l < 3 (2 radius + 1) watches neighbour (band b + l / 3 - radius, column g + l % 3 - 1)
+    // lane l < 3 (2 radius + 1) watches neighbour (band b + l / 3 - radius, column g + l % 3 - 1);
+    // when far, lane 16 + m < 16 + 2 (2 radius + 1) watches (band b + m / 2 - radius, column g -+ 2)
     const int nbands = (p.nr + p.band - 1) / p.band;
     const int lane = threadIdx.x & 31;
     const unsigned *f = nullptr;
@@ -995,6 +998,12 @@ __device__ bool wait_neighbours(const StepParams<C> &p, const unsigned *flags, i
         int gg = g + lane % 3 - 1;
         if (wrap)
             gg = gg < 0 ? gg + cols : (gg >= cols ? gg - cols : gg);
+        if (bb >= 0 && bb < nbands && gg >= 0 && gg < cols)
+            f = flags + bb * cols + gg;
+    } else if (far && lane >= 16 && lane < 16 + 2 * (2 * radius + 1)) {
+        const int bb = b + (lane - 16) / 2 - radius;
+        int gg = g + ((lane & 1) ? 2 : -2);
+        gg = gg < 0 ? gg + cols : (gg >= cols ? gg - cols : gg);
         if (bb >= 0 && bb < nbands && gg >= 0 && gg < cols)
             f = flags + bb * cols + gg;
     }
@@ -1011,7 +1020,27 @@ __device__ bool wait_neighbours(const StepParams<C> &p, const unsigned *flags, i
     }
 }
 
-template <class S, class C>
+// With periodic ends and a last strip of one column (nx - 1 a multiple of
+// the strip width), the pulled moments of column nx - 1 read column nx - 2
+// and the periodic ghost column nx, which strip 0 writes.  The strip before
+// the last one takes them for its right neighbour column, strip 0 for the
+// periodic neighbour of column 0: with four strips or more these tiles are
+// two strips apart across the wrap, so their items also wait for the items
+// two columns out.  The step kernels take this path only in their FAR
+// instantiation, which the host launches for such lattices alone: every
+// other launch runs the one-column wait unchanged.
+__host__ __device__ constexpr bool far_wrap(int bc_in, int nx, int nstrips, int strip_cols)
+{
+    return bc_in == IN_PERIODIC && (nx - 1) % strip_cols == 0 && nstrips >= 4;
+}
+
+template <class C>
+__device__ __forceinline__ bool far_wrap(const StepParams<C> &p)
+{
+    return far_wrap(p.bc_in, p.nx, p.nstrips, 32 * NodesPerLane<C>::value);
+}
+
+template <class S, class C, bool FAR = false>
 __global__ void __launch_bounds__(256) step_run_kernel(const __grid_constant__ StepParams<C> p, const RunCtl ctl)
 {
     constexpr int NV = NodesPerLane<C>::value;
@@ -1043,7 +1072,8 @@ __global__ void __launch_bounds__(256) step_run_kernel(const __grid_constant__ S
         const int k = (int)(n / items);
         const int item = (int)(n - (unsigned)k * items);
         const int b = item / cols, g = item - b * cols;
-        if (k > 0 && !wait_neighbours<C>(p, ctl.flags, cols, ctl.radius, ctl.wrap != 0, b, g, k, ctl.spin_limit)) {
+        if (k > 0 && !wait_neighbours<C>(p, ctl.flags, cols, ctl.radius, ctl.wrap != 0, b, g, k, ctl.spin_limit,
+                                         FAR && far_wrap(p))) {
             if (lane == 0)
                 atomicOr(p.status, STATUS_TIMEOUT);
             break;  // whole warp
@@ -1074,7 +1104,7 @@ struct TileRef {
     int tile;     // warp tile index within that lattice
 };
 
-template <class S, class C>
+template <class S, class C, bool FAR = false>
 __global__ void __launch_bounds__(256) batch_run_kernel(const TileRef *__restrict__ tiles, int ntiles,
                                                         const StepParams<C> *__restrict__ lattices, const RunCtl ctl)
 {
@@ -1106,7 +1136,8 @@ __global__ void __launch_bounds__(256) batch_run_kernel(const TileRef *__restric
         __syncwarp();
         const StepParams<C> &p = *pw;
         if (k > 0 && !wait_neighbours<C>(p, ctl.flags + (idx - t.tile), p.nstrips, ctl.radius, p.bc_in == IN_PERIODIC,
-                                         t.tile / p.nstrips, t.tile % p.nstrips, k, ctl.spin_limit)) {
+                                         t.tile / p.nstrips, t.tile % p.nstrips, k, ctl.spin_limit,
+                                         FAR && far_wrap(p))) {
             if (lane == 0)
                 atomicOr(p.status, STATUS_TIMEOUT);
             break;  // whole warp

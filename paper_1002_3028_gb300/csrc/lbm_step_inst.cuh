@@ -13,31 +13,44 @@ cudaError_t LBM_CAT(launch_run_, LBM_TAG)(const StepParams<LBM_C> &p, const RunC
     if (p.ntiles <= 0 || ctl.nsteps <= 0)
         return cudaSuccess;
     const int smem = run_smem<LBM_S, LBM_C>(warps_per_cta);
-    step_run_kernel<LBM_S, LBM_C><<<ctas, 32 * warps_per_cta, smem, s>>>(p, ctl);
+    if (far_wrap(p.bc_in, p.nx, p.nstrips, 32 * NodesPerLane<LBM_C>::value))
+        step_run_kernel<LBM_S, LBM_C, true><<<ctas, 32 * warps_per_cta, smem, s>>>(p, ctl);
+    else
+        step_run_kernel<LBM_S, LBM_C, false><<<ctas, 32 * warps_per_cta, smem, s>>>(p, ctl);
     return cudaGetLastError();
 }
 
 // allows the dynamic shared memory of the widest CTA and reports how many
-// CTAs of the given width fit on one SM
+// CTAs of the given width fit on one SM (the fewer of the two instantiations)
 cudaError_t LBM_CAT(occupancy_run_, LBM_TAG)(int warps_per_cta, int *ctas_per_sm)
 {
-    cudaError_t e = cudaFuncSetAttribute(step_run_kernel<LBM_S, LBM_C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         run_smem<LBM_S, LBM_C>(8));
-    if (e != cudaSuccess)
-        return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, step_run_kernel<LBM_S, LBM_C>,
-                                                         32 * warps_per_cta, run_smem<LBM_S, LBM_C>(warps_per_cta));
+    int n[2] = {0, 0};
+    for (int far = 0; far < 2; ++far) {
+        const void *fn = far ? reinterpret_cast<const void *>(step_run_kernel<LBM_S, LBM_C, true>)
+                             : reinterpret_cast<const void *>(step_run_kernel<LBM_S, LBM_C, false>);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, run_smem<LBM_S, LBM_C>(8));
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[far], fn, 32 * warps_per_cta,
+                                                              run_smem<LBM_S, LBM_C>(warps_per_cta));
+        if (e != cudaSuccess)
+            return e;
+    }
+    *ctas_per_sm = n[0] < n[1] ? n[0] : n[1];
+    return cudaSuccess;
 }
 
 // nsteps steps of every member lattice in one persistent launch, then the
 // device-side advance of the parameter table
 cudaError_t LBM_CAT(launch_batch_, LBM_TAG)(const TileRef *tiles, int ntiles, StepParams<LBM_C> *lattices, int nlat,
-                                            const RunCtl &ctl, int warps_per_cta, int ctas, cudaStream_t s)
+                                            const RunCtl &ctl, int warps_per_cta, int ctas, int far, cudaStream_t s)
 {
     if (ntiles <= 0 || nlat <= 0 || ctl.nsteps <= 0)
         return cudaSuccess;
     const int smem = warps_per_cta * batch_smem_per_warp<LBM_S, LBM_C>();
-    batch_run_kernel<LBM_S, LBM_C><<<ctas, 32 * warps_per_cta, smem, s>>>(tiles, ntiles, lattices, ctl);
+    if (far)
+        batch_run_kernel<LBM_S, LBM_C, true><<<ctas, 32 * warps_per_cta, smem, s>>>(tiles, ntiles, lattices, ctl);
+    else
+        batch_run_kernel<LBM_S, LBM_C, false><<<ctas, 32 * warps_per_cta, smem, s>>>(tiles, ntiles, lattices, ctl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
@@ -47,14 +60,20 @@ cudaError_t LBM_CAT(launch_batch_, LBM_TAG)(const TileRef *tiles, int ntiles, St
 
 cudaError_t LBM_CAT(occupancy_batch_, LBM_TAG)(int warps_per_cta, int *ctas_per_sm)
 {
-    cudaError_t e = cudaFuncSetAttribute(batch_run_kernel<LBM_S, LBM_C>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         8 * batch_smem_per_warp<LBM_S, LBM_C>());
-    if (e != cudaSuccess)
-        return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, batch_run_kernel<LBM_S, LBM_C>,
-                                                         32 * warps_per_cta,
-                                                         warps_per_cta * batch_smem_per_warp<LBM_S, LBM_C>());
+    int n[2] = {0, 0};
+    for (int far = 0; far < 2; ++far) {
+        const void *fn = far ? reinterpret_cast<const void *>(batch_run_kernel<LBM_S, LBM_C, true>)
+                             : reinterpret_cast<const void *>(batch_run_kernel<LBM_S, LBM_C, false>);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             8 * batch_smem_per_warp<LBM_S, LBM_C>());
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[far], fn, 32 * warps_per_cta,
+                                                              warps_per_cta * batch_smem_per_warp<LBM_S, LBM_C>());
+        if (e != cudaSuccess)
+            return e;
+    }
+    *ctas_per_sm = n[0] < n[1] ? n[0] : n[1];
+    return cudaSuccess;
 }
 
 cudaError_t LBM_CAT(launch_fields_, LBM_TAG)(const StepParams<LBM_C> &p, void *out, int out_f64, cudaStream_t s)
