@@ -9,7 +9,9 @@ lattices are compared bit for bit, in both memory patterns:
 - every boundary set, and the four storage types;
 - random bands, warps per CTA and item groups.
 One lattice is also wide enough that the AA schedule must widen its items
-to keep one band of items resident.
+to keep one band of items resident.  Batches of random members, in both
+patterns, go through a graph replay and a remainder launch, and each member
+must equal its own one-step launches.
 """
 import random
 
@@ -95,3 +97,29 @@ def test_aa_widens_items_on_a_lattice_wider_than_the_resident_warps(lbm, orc):
     want = run(lbm, orc, w, "f32", "ab", 0, 0, 0, [1] * 6, 3)
     got = run(lbm, orc, w, "f32", "aa", 0, 0, 0, [6], 3)
     assert torch.equal(got, want)
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_batch_members_equal_one_step_launches_alone(lbm, orc, seed, pattern):
+    """A batch of 3-9 random members (one storage type) stepped through a graph replay of
+    64 steps and a remainder launch: every member equals its own one-step launches."""
+    rng = random.Random(1000 + seed)
+    storage = rng.choice(["f64", "f32", "f16"])
+    strip = 32 if storage == "f64" else 64
+    batch = lbm.Batch(storage)
+    members = []
+    for m in range(rng.randint(3, 9)):
+        nx = rng.choice([rng.randint(1, 300), strip * rng.randint(1, 5) + 1])
+        nr = rng.choice([rng.randint(1, 80), rng.randint(1, 6)])
+        w = workload(nx, nr, dict(rng.choice(BOUNDARIES)))
+        want = run(lbm, orc, w, storage, "ab", 0, 0, 0, [1] * 70, 77 + m)
+        lat = lbm.Lattice.from_workload(w, storage, pattern=pattern)
+        f0, g0 = I.random_state(nx, nr, orc.feq(1.0, 0.02, 0.0), orc.geq(1.2, 0.02, 0.0), 0.05, 77 + m)
+        lat.set_state(f0, g0, 2)
+        batch.add(lat)
+        members.append((lat, want))
+    batch.step(70, graph=True)
+    for lat, want in members:
+        assert lat.check() == 0
+        assert torch.equal(lat.save()[0], want), (pattern, storage, lat.nx, lat.nr)
