@@ -292,3 +292,30 @@ def test_aa_serving_engine_admits_by_aa_size(lbm):
     lat = aa.admit(req)
     aa.step(10)
     assert lat.step_count == 10 and lat.check() == 0
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_aa_lattice_joins_and_leaves_a_batch_in_either_representation(lbm, orc, storage):
+    """Members join after odd and even step counts of their own (so in either representation),
+    run in the batch, then leave and step alone again: all equal two-buffer lattices alone."""
+    pairs = []
+    batch = lbm.Batch(storage)
+    for m, (bname, alone) in enumerate([("jet", 3), ("periodic_axis", 4), ("substrate", 5)]):
+        ab, aa = twins(lbm, orc, workload(150, 45, **BOUNDARIES[bname]), storage, seed=60 + m)
+        ab.step(alone)
+        aa.step(alone)
+        batch.add(aa)
+        pairs.append((ab, aa))
+    batch.step(67, graph=True)
+    for ab, _ in pairs:
+        ab.step(67)
+    for ab, aa in pairs:
+        assert_same(ab, aa)
+    batch.remove(pairs[0][1])
+    pairs[0][1].step(9)
+    pairs[0][0].step(9)
+    batch.step(2)
+    for ab, _ in pairs[1:]:
+        ab.step(2)
+    for ab, aa in pairs:
+        assert_same(ab, aa)
