@@ -1,12 +1,14 @@
 """The AA pattern (one population buffer updated in place) against the two-buffer path and the oracle.
 
 Both patterns apply the same arithmetic to the same stored values in the same
-order; only where a value is kept differs.  So every result of an AA lattice
-(stored populations, fields, diagnostics, checkpoints) must equal the
-two-buffer lattice's bit for bit, after odd and even step counts (the two
-representations of the AA state), for every boundary kind, storage type,
-launch shape and item group.  FP64 AA steps are also compared with the
-oracle directly, at its 1e-12 bar.
+order; only where a value is kept differs.  Every result of an AA lattice must
+therefore equal the two-buffer lattice's bit for bit: stored populations,
+fields, checkpoints, and the diagnostics except the steady residual, which an
+AA lattice cannot form since it keeps no previous state.  This must hold
+after odd and even step counts (the two representations of the AA state),
+for every boundary kind, storage type, launch shape and item group, alone and
+in batches.  FP64 AA steps are also compared with the oracle directly, at its
+1e-12 bar.
 """
 import math
 import os
