@@ -241,7 +241,12 @@ LBM_API int lbm_check(lbm_lattice *h, int32_t *flags);
  * raises LBM_STATUS_TIMEOUT and its warp stops; nothing is computed or
  * written, and the lattice's state and step count are unchanged.  Writes
  * the status read back (LBM_STATUS_TIMEOUT when the waits behaved) to
- * *flags and clears it.  Synchronises the device.  Not for batch members.
+ * *flags and clears it.  For LBM_PATTERN_AA lattices of two or more work
+ * items a second launch also tests the wait in the middle of an item: one
+ * item forms and publishes its edge moments (scratch that the next step
+ * recomputes) and waits for neighbours that never run; *flags is
+ * LBM_STATUS_TIMEOUT only if both launches raised it.  Synchronises the
+ * device.  Not for batch members.
  */
 LBM_API int lbm_selftest_wait_timeout(lbm_lattice *h, int32_t *flags);
 
