@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -31,6 +32,84 @@ int fail(int code, const char *fmt, ...)
 int cuda_fail(cudaError_t e, const char *what)
 {
     return fail(LBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ---- host-to-device uploads without synchronisation ---------------------------
+// Inlet profiles, property tables and batch tables are copied through pinned
+// staging blocks (a ring per device), so cudaMemcpyAsync never has to stage
+// pageable memory itself, which may synchronise the stream and so drain the
+// work queued on it.  A block is reused once the copy that last read it has
+// completed (its event).  An upload larger than a block takes the pageable
+// path and synchronises its stream.
+constexpr size_t kStageBytes = (size_t)1 << 20;
+constexpr int kStageBlocks = 16;
+constexpr int kMaxDevices = 64;
+
+struct StageBlock {
+    char *host = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
+std::mutex g_stage_mutex;
+StageBlock g_stage[kMaxDevices][kStageBlocks];
+int g_stage_next[kMaxDevices] = {};
+
+struct Part {
+    void *dst;
+    const void *src;
+    size_t n;
+};
+
+size_t round16(size_t n) { return (n + 15) / 16 * 16; }
+
+// copies every part (host source, device destination) in the order of stream s
+cudaError_t upload(const Part *parts, int nparts, cudaStream_t s)
+{
+    size_t total = 0;
+    for (int k = 0; k < nparts; ++k)
+        total += round16(parts[k].n);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (total > kStageBytes || dev < 0 || dev >= kMaxDevices) {
+        for (int k = 0; k < nparts && e == cudaSuccess; ++k)
+            if (parts[k].n > 0)
+                e = cudaMemcpyAsync(parts[k].dst, parts[k].src, parts[k].n, cudaMemcpyHostToDevice, s);
+        return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+    }
+    std::lock_guard<std::mutex> lock(g_stage_mutex);
+    StageBlock &b = g_stage[dev][g_stage_next[dev]];
+    g_stage_next[dev] = (g_stage_next[dev] + 1) % kStageBlocks;
+    if (!b.host) {
+        e = cudaHostAlloc(reinterpret_cast<void **>(&b.host), kStageBytes, cudaHostAllocPortable);
+        if (e != cudaSuccess) {
+            b.host = nullptr;
+            return e;
+        }
+        e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            cudaFreeHost(b.host);
+            b.host = nullptr;
+            b.done = nullptr;
+            return e;
+        }
+    } else {
+        e = cudaEventSynchronize(b.done);  // the copies that last read this block have run
+        if (e != cudaSuccess)
+            return e;
+    }
+    size_t off = 0;
+    for (int k = 0; k < nparts && e == cudaSuccess; ++k) {
+        if (parts[k].n == 0)
+            continue;
+        std::memcpy(b.host + off, parts[k].src, parts[k].n);
+        e = cudaMemcpyAsync(parts[k].dst, b.host + off, parts[k].n, cudaMemcpyHostToDevice, s);
+        off += round16(parts[k].n);
+    }
+    if (e == cudaSuccess)
+        e = cudaEventRecord(b.done, s);
+    return e;
 }
 
 constexpr int kMaxTable = 4096;
@@ -160,6 +239,8 @@ struct lbm_lattice {
     int device, sms;
     bool aa;               // AA pattern: one buffer (cur stays 0) and the tiles' edge moments
     int phase;             // AA pattern: representation of the stored state (lbm_aa.cuh)
+    cudaEvent_t ready;     // recorded after the set-up work lbm_create enqueued
+    cudaEvent_t last;      // recorded after the last work enqueued on the lattice
 
     void *buf(int b) const { return mem + L.off_buf[b]; }
     template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(mem + off); }
@@ -185,6 +266,8 @@ struct lbm_batch {
     cudaStream_t capture;  // private stream used to capture step graphs
     cudaGraphExec_t graph;
     int graph_version, graph_steps;
+    cudaEvent_t last;  // recorded after the last batch launch
+    bool launched;     // `last` has been recorded
 };
 
 namespace {
@@ -386,19 +469,33 @@ int upload_pair(lbm_lattice *h, size_t off_d, size_t off_f, const double *src, i
     std::vector<float> tmp((size_t)n);
     for (int k = 0; k < n; ++k)
         tmp[(size_t)k] = (float)src[k];
-    cudaError_t e = cudaMemcpyAsync(h->mem + off_d, src, (size_t)n * 8, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->mem + off_f, tmp.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s);
-    // the float staging vector is pageable: the copy has been staged when the call returns,
-    // but synchronise anyway so the vector can be released safely on every driver
-    if (e == cudaSuccess)
-        e = cudaStreamSynchronize(s);
+    const Part parts[2] = {{h->mem + off_d, src, (size_t)n * 8}, {h->mem + off_f, tmp.data(), (size_t)n * 4}};
+    cudaError_t e = upload(parts, 2, s);
     if (e != cudaSuccess)
         return cuda_fail(e, what);
     return LBM_OK;
 }
 
 bool valid(const lbm_lattice *h) { return h != nullptr && h->mem != nullptr; }
+
+// Work that a call enqueues on stream s comes after the lattice's set-up
+// (enter) and is remembered as the lattice's last use (leave), after which
+// lbm_destroy releases memory the library allocated.
+int enter(const lbm_lattice *h, cudaStream_t s)
+{
+    cudaError_t e = cudaStreamWaitEvent(s, h->ready, 0);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "ordering the stream after the lattice's set-up");
+}
+
+int leave(lbm_lattice *h, cudaStream_t s, int rc)
+{
+    if (rc == LBM_OK) {
+        cudaError_t e = cudaEventRecord(h->last, s);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "recording the lattice's last use");
+    }
+    return rc;
+}
 
 }  // namespace
 
@@ -496,23 +593,25 @@ int batch_rebuild(lbm_batch *b, cudaStream_t s)
         return fail(LBM_ERR_INVALID_ARG, "too many tiles in the batch");
     cudaError_t e = cudaSuccess;
     if (params.size() > b->cap_params || tiles.size() > b->cap_tiles) {
-        drop_graph(b);
-        cudaStreamSynchronize(s);  // the old tables may still be read by queued steps
+        // the old tables may still be read by queued steps: they are released in stream order
         if (params.size() > b->cap_params) {
-            cudaFree(b->d_params);
+            if (b->d_params)
+                cudaFreeAsync(b->d_params, s);
             b->d_params = nullptr;
-            e = cudaMalloc(&b->d_params, params.size() * 2);
+            e = cudaMallocAsync(&b->d_params, params.size() * 2, s);
             b->cap_params = e == cudaSuccess ? params.size() * 2 : 0;
         }
         if (e == cudaSuccess && tiles.size() > b->cap_tiles) {
-            cudaFree(b->d_tiles);
-            cudaFree(b->d_sync);
+            if (b->d_tiles)
+                cudaFreeAsync(b->d_tiles, s);
+            if (b->d_sync)
+                cudaFreeAsync(b->d_sync, s);
             b->d_tiles = nullptr;
             b->d_sync = nullptr;
             const size_t cap = std::max<size_t>(1, tiles.size() * 2);
-            e = cudaMalloc(&b->d_tiles, cap * sizeof(lbm::TileRef));
+            e = cudaMallocAsync(&b->d_tiles, cap * sizeof(lbm::TileRef), s);
             if (e == cudaSuccess)
-                e = cudaMalloc(&b->d_sync, (2 * cap + 1) * sizeof(unsigned));
+                e = cudaMallocAsync(&b->d_sync, (2 * cap + 1) * sizeof(unsigned), s);
             b->cap_tiles = e == cudaSuccess ? cap : 0;
         }
         if (e != cudaSuccess) {
@@ -520,12 +619,17 @@ int batch_rebuild(lbm_batch *b, cudaStream_t s)
             return fail(LBM_ERR_OOM, "batch table allocation: %s", cudaGetErrorString(e));
         }
     }
-    if (n > 0)
-        e = cudaMemcpyAsync(b->d_params, params.data(), params_size(b->storage) * (size_t)n, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && !tiles.empty())
-        e = cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(lbm::TileRef), cudaMemcpyHostToDevice, s);
+    const Part parts[2] = {{b->d_params, params.data(), params_size(b->storage) * (size_t)n},
+                           {b->d_tiles, tiles.data(), tiles.size() * sizeof(lbm::TileRef)}};
+    e = upload(parts, 2, s);
     if (e != cudaSuccess)
         return cuda_fail(e, "batch table upload");
+    // the new members' set-up comes first
+    for (lbm_lattice *h : b->members) {
+        int rc2 = enter(h, s);
+        if (rc2)
+            return rc2;
+    }
     b->ntiles = (int)tiles.size();
     b->ctas_max = per_sm * std::max(1, b->sms);
     b->dirty = false;
@@ -537,7 +641,7 @@ int batch_rebuild(lbm_batch *b, cudaStream_t s)
 cudaError_t batch_launch(lbm_batch *b, int nsteps, cudaStream_t s)
 {
     const int n = (int)b->members.size();
-    cudaError_t e = cudaMemsetAsync(b->d_sync, 0, (size_t)((b->aa ? 2 : 1) * b->ntiles + 1) * sizeof(unsigned), s);
+    cudaError_t e = cudaMemsetAsync(b->d_sync, 0, (2 * b->cap_tiles + 1) * sizeof(unsigned), s);
     if (e != cudaSuccess)
         return e;
     lbm::RunCtl ctl;
@@ -589,12 +693,14 @@ int64_t batch_steps_per_launch(const lbm_batch *b)
     return std::max<int64_t>(1, ((int64_t)1 << 31) / std::max<int64_t>(1, 2 * (int64_t)b->ntiles));
 }
 
-// instantiate (once per table version) a graph of one launch of kGraphSteps steps
+// a graph of one launch of kGraphSteps steps, captured once per table
+// version; the executable graph is updated in place (launches already queued
+// keep their parameters), or re-instantiated once the batch's queued work
+// has run if the update is refused
 int batch_graph(lbm_batch *b)
 {
     if (b->graph && b->graph_version == b->version)
         return LBM_OK;
-    drop_graph(b);
     cudaGraph_t g = nullptr;
     const int steps = (int)std::min<int64_t>(kGraphSteps, batch_steps_per_launch(b));
     cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
@@ -603,7 +709,18 @@ int batch_graph(lbm_batch *b)
     cudaError_t e2 = cudaStreamEndCapture(b->capture, &g);
     if (e == cudaSuccess)
         e = e2;
-    if (e == cudaSuccess)
+    bool updated = false;
+    if (e == cudaSuccess && b->graph) {
+        cudaGraphExecUpdateResultInfo info;
+        updated = cudaGraphExecUpdate(b->graph, g, &info) == cudaSuccess;
+        if (!updated) {
+            cudaGetLastError();
+            if (b->launched)
+                cudaEventSynchronize(b->last);
+            drop_graph(b);
+        }
+    }
+    if (e == cudaSuccess && !updated)
         e = cudaGraphInstantiate(&b->graph, g, 0);
     if (g)
         cudaGraphDestroy(g);
@@ -670,6 +787,10 @@ int lattice_view(const lbm_lattice *h, LatticeView *out)
 
 int api_fail(int code, const char *msg) { return fail(code, "%s", msg); }
 
+int lattice_enter(const lbm_lattice *h, cudaStream_t s) { return enter(h, s); }
+
+int lattice_leave(lbm_lattice *h, cudaStream_t s, int rc) { return leave(h, s, rc); }
+
 int diag_finish(const double *v, int have_prev, lbm_diag *out) { return finish_diag(v, have_prev, out); }
 
 }  // namespace lbm
@@ -720,26 +841,45 @@ int lbm_create(const lbm_desc *d, void *dev_mem, size_t bytes, lbm_lattice **out
     cudaGetDevice(&h->device);
     h->sms = 1;
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    // Set-up is enqueued on the legacy default stream with no host
+    // synchronisation: work of other streams is ordered after it through the
+    // `ready` event (enter), so creating a lattice never drains the device.
+    cudaStream_t s0 = nullptr;
+    h->ready = h->last = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&h->ready, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&h->last, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        if (h->ready)
+            cudaEventDestroy(h->ready);
+        delete h;
+        cudaGetLastError();
+        return cuda_fail(e, "creating the lattice's events");
+    }
+    auto undo = [&]() {
+        if (h->own)
+            cudaFreeAsync(h->mem, s0);
+        cudaEventDestroy(h->ready);
+        cudaEventDestroy(h->last);
+        delete h;
+    };
     if (h->own) {
         void *p = nullptr;
-        cudaError_t e = cudaMalloc(&p, L.total);
+        e = cudaMallocAsync(&p, L.total, s0);
         if (e != cudaSuccess) {
-            delete h;
+            h->own = false;
+            undo();
             cudaGetLastError();
-            return fail(LBM_ERR_OOM, "cudaMalloc of %zu bytes: %s", L.total, cudaGetErrorString(e));
+            return fail(LBM_ERR_OOM, "cudaMallocAsync of %zu bytes: %s", L.total, cudaGetErrorString(e));
         }
         h->mem = static_cast<char *>(p);
     } else {
         h->mem = static_cast<char *>(dev_mem);
     }
     // rest state: every stored deviation is zero
-    cudaError_t e = cudaMemset(h->mem, 0, L.total);
-    if (e == cudaSuccess)
-        e = cudaDeviceSynchronize();
+    e = cudaMemsetAsync(h->mem, 0, L.total, s0);
     if (e != cudaSuccess) {
-        if (h->own)
-            cudaFree(h->mem);
-        delete h;
+        undo();
         return cuda_fail(e, "initialising lattice memory");
     }
     // defaults: no inflow, T_in = T0, nu = alpha = 0.1 on [T0, T0 + 1]
@@ -748,23 +888,23 @@ int lbm_create(const lbm_desc *d, void *dev_mem, size_t bytes, lbm_lattice **out
     h->ntab = 1;
     h->T_lo = d->T0;
     h->T_hi = d->T0 + 1.0;
-    rc = upload_pair(h, L.off_uin_d, L.off_uin_f, zeros.data(), d->nr, nullptr, "inlet upload");
-    if (!rc) rc = upload_pair(h, L.off_tin_d, L.off_tin_f, tin.data(), d->nr, nullptr, "inlet upload");
-    if (!rc) rc = upload_pair(h, L.off_nu_d, L.off_nu_f, &one, 1, nullptr, "table upload");
-    if (!rc) rc = upload_pair(h, L.off_al_d, L.off_al_f, &one, 1, nullptr, "table upload");
+    rc = upload_pair(h, L.off_uin_d, L.off_uin_f, zeros.data(), d->nr, s0, "inlet upload");
+    if (!rc) rc = upload_pair(h, L.off_tin_d, L.off_tin_f, tin.data(), d->nr, s0, "inlet upload");
+    if (!rc) rc = upload_pair(h, L.off_nu_d, L.off_nu_f, &one, 1, s0, "table upload");
+    if (!rc) rc = upload_pair(h, L.off_al_d, L.off_al_f, &one, 1, s0, "table upload");
     if (!rc)
         rc = plan_launch(h);
     if (!rc)
-        rc = fill_ghosts(h, nullptr);
+        rc = fill_ghosts(h, s0);
     if (!rc) {
-        cudaError_t e2 = cudaDeviceSynchronize();
-        if (e2 != cudaSuccess)
-            rc = cuda_fail(e2, "initialising ghosts");
+        e = cudaEventRecord(h->ready, s0);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(h->last, s0);
+        if (e != cudaSuccess)
+            rc = cuda_fail(e, "recording the end of the set-up");
     }
     if (rc) {
-        if (h->own)
-            cudaFree(h->mem);
-        delete h;
+        undo();
         return rc;
     }
     *out = h;
@@ -778,14 +918,17 @@ void lbm_destroy(lbm_lattice *h)
     if (h->batch)
         lbm_batch_remove(h->batch, h);
     if (h->own && h->mem) {
-        cudaDeviceSynchronize();
-        cudaFree(h->mem);
+        // released in stream order after the lattice's last use: no host synchronisation
+        cudaStreamWaitEvent(nullptr, h->last, 0);
+        cudaFreeAsync(h->mem, nullptr);
     }
     h->mem = nullptr;
+    cudaEventDestroy(h->ready);
+    cudaEventDestroy(h->last);
     delete h;
 }
 
-int lbm_set_inlet(lbm_lattice *h, const double *u_in, const double *T_in, int32_t nr, lbm_stream stream)
+static int set_inlet_impl(lbm_lattice *h, const double *u_in, const double *T_in, int32_t nr, lbm_stream stream)
 {
     if (!valid(h) || !u_in || !T_in)
         return fail(LBM_ERR_INVALID_ARG, "bad handle or NULL profile");
@@ -805,7 +948,7 @@ int lbm_set_inlet(lbm_lattice *h, const double *u_in, const double *T_in, int32_
     return rc;
 }
 
-int lbm_set_properties(lbm_lattice *h, const double *nu, const double *alpha, int32_t n, double T_lo, double T_hi,
+static int set_properties_impl(lbm_lattice *h, const double *nu, const double *alpha, int32_t n, double T_lo, double T_hi,
                        lbm_stream stream)
 {
     if (!valid(h) || !nu || !alpha)
@@ -831,7 +974,7 @@ int lbm_set_properties(lbm_lattice *h, const double *nu, const double *alpha, in
     return LBM_OK;
 }
 
-int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
+static int step_impl(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
 {
     if (!valid(h) || nsteps < 0)
         return fail(LBM_ERR_INVALID_ARG, "bad handle or negative step count");
@@ -993,7 +1136,7 @@ int32_t lbm_get_item_group(const lbm_lattice *h) { return valid(h) ? item_group(
 
 int64_t lbm_get_step(const lbm_lattice *h) { return valid(h) ? h->step : -1; }
 
-int lbm_diagnostics(lbm_lattice *h, lbm_diag *out, lbm_stream stream)
+static int diagnostics_impl(lbm_lattice *h, lbm_diag *out, lbm_stream stream)
 {
     if (!valid(h) || !out)
         return fail(LBM_ERR_INVALID_ARG, "bad handle or NULL output");
@@ -1035,7 +1178,7 @@ int lbm_check(lbm_lattice *h, int32_t *flags)
     return LBM_OK;
 }
 
-int lbm_get_fields(lbm_lattice *h, void *dev_out, int32_t out_type, lbm_stream stream)
+static int get_fields_impl(lbm_lattice *h, void *dev_out, int32_t out_type, lbm_stream stream)
 {
     if (!valid(h) || !dev_out)
         return fail(LBM_ERR_INVALID_ARG, "bad handle or NULL output");
@@ -1053,7 +1196,7 @@ int lbm_get_fields(lbm_lattice *h, void *dev_out, int32_t out_type, lbm_stream s
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "fields kernel launch");
 }
 
-int lbm_get_state(lbm_lattice *h, double *dev_f, double *dev_g, lbm_stream stream)
+static int get_state_impl(lbm_lattice *h, double *dev_f, double *dev_g, lbm_stream stream)
 {
     if (!valid(h) || !dev_f || !dev_g)
         return fail(LBM_ERR_INVALID_ARG, "bad handle or NULL output");
@@ -1079,7 +1222,7 @@ int lbm_get_state(lbm_lattice *h, double *dev_f, double *dev_g, lbm_stream strea
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "state read kernel launch");
 }
 
-int lbm_set_state(lbm_lattice *h, const double *dev_f, const double *dev_g, int64_t step, lbm_stream stream)
+static int set_state_impl(lbm_lattice *h, const double *dev_f, const double *dev_g, int64_t step, lbm_stream stream)
 {
     if (!valid(h) || !dev_f || !dev_g || step < 0)
         return fail(LBM_ERR_INVALID_ARG, "bad handle, NULL input or negative step");
@@ -1145,14 +1288,14 @@ static int copy_planes(lbm_lattice *h, void *dense, bool out, cudaStream_t s)
     return LBM_OK;
 }
 
-int lbm_save(lbm_lattice *h, void *dev_out, lbm_stream stream)
+static int save_impl(lbm_lattice *h, void *dev_out, lbm_stream stream)
 {
     if (!valid(h) || !dev_out)
         return fail(LBM_ERR_INVALID_ARG, "bad handle or NULL output");
     return copy_planes(h, dev_out, true, static_cast<cudaStream_t>(stream));
 }
 
-int lbm_restore(lbm_lattice *h, const void *dev_in, int64_t step, lbm_stream stream)
+static int restore_impl(lbm_lattice *h, const void *dev_in, int64_t step, lbm_stream stream)
 {
     if (!valid(h) || !dev_in || step < 0)
         return fail(LBM_ERR_INVALID_ARG, "bad handle, NULL input or negative step");
@@ -1207,10 +1350,16 @@ int lbm_batch_create(int32_t storage, lbm_batch **out)
     b->sms = 1;
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        e = cudaEventCreateWithFlags(&b->last, cudaEventDisableTiming);
+        if (e != cudaSuccess)
+            cudaStreamDestroy(b->capture);
+    }
     if (e != cudaSuccess) {
         delete b;
         return cuda_fail(e, "creating the capture stream");
     }
+    b->launched = false;
     *out = b;
     return LBM_OK;
 }
@@ -1219,14 +1368,16 @@ void lbm_batch_destroy(lbm_batch *b)
 {
     if (!b)
         return;
-    cudaDeviceSynchronize();
+    if (b->launched)
+        cudaEventSynchronize(b->last);  // the batch's own queued launches, not the whole device
     for (lbm_lattice *h : b->members)
         h->batch = nullptr;
     drop_graph(b);
-    cudaFree(b->d_params);
-    cudaFree(b->d_tiles);
-    cudaFree(b->d_sync);
+    for (void *p : {b->d_params, static_cast<void *>(b->d_tiles), static_cast<void *>(b->d_sync)})
+        if (p)
+            cudaFreeAsync(p, nullptr);
     cudaStreamDestroy(b->capture);
+    cudaEventDestroy(b->last);
     delete b;
 }
 
@@ -1257,6 +1408,13 @@ int lbm_batch_remove(lbm_batch *b, lbm_lattice *h)
         }
     h->batch = nullptr;
     b->dirty = true;
+    if (b->launched) {  // the lattice's last use is the batch's last launch
+        cudaError_t e = cudaStreamWaitEvent(nullptr, b->last, 0);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(h->last, nullptr);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "recording the lattice's last use");
+    }
     return LBM_OK;
 }
 
@@ -1321,7 +1479,98 @@ int lbm_batch_step(lbm_batch *b, int32_t nsteps, int32_t use_graph, lbm_stream s
         done += m;
     }
     batch_advance_host(b, nsteps);
+    cudaError_t e = cudaEventRecord(b->last, s);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "recording the batch's last launch");
+    b->launched = true;
     return LBM_OK;
+}
+
+
+// The entry points that enqueue work on a caller's stream: the stream is
+// first ordered after the lattice's set-up, and the call's work is then
+// recorded as the lattice's last use.
+
+int lbm_set_inlet(lbm_lattice *h, const double *u_in, const double *T_in, int32_t nr, lbm_stream stream)
+{
+    if (!valid(h))
+        return fail(LBM_ERR_INVALID_ARG, "bad lattice handle");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int rc = enter(h, s);
+    return rc ? rc : leave(h, s, set_inlet_impl(h, u_in, T_in, nr, stream));
+}
+
+int lbm_set_properties(lbm_lattice *h, const double *nu, const double *alpha, int32_t n, double T_lo, double T_hi,
+                       lbm_stream stream)
+{
+    if (!valid(h))
+        return fail(LBM_ERR_INVALID_ARG, "bad lattice handle");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int rc = enter(h, s);
+    return rc ? rc : leave(h, s, set_properties_impl(h, nu, alpha, n, T_lo, T_hi, stream));
+}
+
+int lbm_step(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
+{
+    if (!valid(h))
+        return fail(LBM_ERR_INVALID_ARG, "bad lattice handle");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int rc = enter(h, s);
+    return rc ? rc : leave(h, s, step_impl(h, nsteps, stream));
+}
+
+int lbm_get_fields(lbm_lattice *h, void *dev_out, int32_t out_type, lbm_stream stream)
+{
+    if (!valid(h))
+        return fail(LBM_ERR_INVALID_ARG, "bad lattice handle");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int rc = enter(h, s);
+    return rc ? rc : leave(h, s, get_fields_impl(h, dev_out, out_type, stream));
+}
+
+int lbm_get_state(lbm_lattice *h, double *dev_f, double *dev_g, lbm_stream stream)
+{
+    if (!valid(h))
+        return fail(LBM_ERR_INVALID_ARG, "bad lattice handle");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int rc = enter(h, s);
+    return rc ? rc : leave(h, s, get_state_impl(h, dev_f, dev_g, stream));
+}
+
+int lbm_set_state(lbm_lattice *h, const double *dev_f, const double *dev_g, int64_t step, lbm_stream stream)
+{
+    if (!valid(h))
+        return fail(LBM_ERR_INVALID_ARG, "bad lattice handle");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int rc = enter(h, s);
+    return rc ? rc : leave(h, s, set_state_impl(h, dev_f, dev_g, step, stream));
+}
+
+int lbm_save(lbm_lattice *h, void *dev_out, lbm_stream stream)
+{
+    if (!valid(h))
+        return fail(LBM_ERR_INVALID_ARG, "bad lattice handle");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int rc = enter(h, s);
+    return rc ? rc : leave(h, s, save_impl(h, dev_out, stream));
+}
+
+int lbm_restore(lbm_lattice *h, const void *dev_in, int64_t step, lbm_stream stream)
+{
+    if (!valid(h))
+        return fail(LBM_ERR_INVALID_ARG, "bad lattice handle");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int rc = enter(h, s);
+    return rc ? rc : leave(h, s, restore_impl(h, dev_in, step, stream));
+}
+
+int lbm_diagnostics(lbm_lattice *h, lbm_diag *out, lbm_stream stream)
+{
+    if (!valid(h))
+        return fail(LBM_ERR_INVALID_ARG, "bad lattice handle");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int rc = enter(h, s);
+    return rc ? rc : leave(h, s, diagnostics_impl(h, out, stream));
 }
 
 }  // extern "C"

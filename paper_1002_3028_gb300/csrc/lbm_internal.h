@@ -58,6 +58,10 @@ struct LatticeView {
     StepParams<float> pf;
 };
 int lattice_view(const lbm_lattice *h, LatticeView *out);
+// orders stream s after the lattice's set-up / records the call's work on s
+// as the lattice's last use (returns rc, or an error of the record)
+int lattice_enter(const lbm_lattice *h, cudaStream_t s);
+int lattice_leave(lbm_lattice *h, cudaStream_t s, int rc);
 int api_fail(int code, const char *msg);                       // sets lbm_last_error
 int diag_finish(const double *v, int have_prev, lbm_diag *out); // fills lbm_diag from folded slots
 

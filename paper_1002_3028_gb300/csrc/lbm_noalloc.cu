@@ -97,6 +97,9 @@ extern "C" int lbm_diagnostics_noalloc(lbm_lattice *h, lbm_diag *out, lbm_stream
     if (rc)
         return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    rc = lattice_enter(h, s);
+    if (rc)
+        return rc;
     switch (v.storage) {
     case LBM_F64: e = launch_rows<double, double>(v.pd, v.prev_valid, scratch, s); break;
     case LBM_F32: e = launch_rows<float, float>(v.pf, v.prev_valid, scratch, s); break;
@@ -112,5 +115,8 @@ extern "C" int lbm_diagnostics_noalloc(lbm_lattice *h, lbm_diag *out, lbm_stream
         cudaGetLastError();
         return api_fail(LBM_ERR_CUDA, "lbm_diagnostics_noalloc: a launch or the result copy failed");
     }
+    rc = lattice_leave(h, s, LBM_OK);
+    if (rc)
+        return rc;
     return diag_finish(vals, v.prev_valid, out);
 }

@@ -84,17 +84,30 @@ class Engine:
     def fields(self, token):
         return None
 
+    def fence(self):
+        """A marker of the work enqueued so far (None when steps run synchronously)."""
+        return None
+
+    def wait(self, fence) -> None:
+        """Block until the work before `fence` has run."""
+
 
 def serve(requests: List[Request], engine: Engine, budget_bytes: float, chunk: int = 256,
           clock: Callable[[], float] = time.perf_counter, sleep: Callable[[float], None] = time.sleep,
-          keep_fields: bool = False) -> ServeStats:
-    """Run a request stream to completion; arrival times are relative to the start."""
+          keep_fields: bool = False, ahead: int = 2) -> ServeStats:
+    """Run a request stream to completion; arrival times are relative to the start.
+
+    The host runs at most `ahead` chunks ahead of the device: before enqueuing
+    another chunk it waits for the chunk `ahead` back, so arrivals are admitted
+    at device time, not behind a long queue of enqueued steps.
+    """
     t0 = clock()
     pending = collections.deque(sorted(requests, key=lambda r: r.arrival_s))
     waiting: collections.deque = collections.deque()
     active: Dict[int, list] = {}  # rid -> [handle, remaining, request, admitted_s, bytes]
     retiring: Dict[int, list] = {}  # rid -> [token, request, admitted_s, bytes]
     results: List[Result] = []
+    fences: collections.deque = collections.deque()
     used = 0.0
     lups = 0.0
     for r in requests:
@@ -120,6 +133,9 @@ def serve(requests: List[Request], engine: Engine, budget_bytes: float, chunk: i
         if active:
             n = min(chunk, min(a[1] for a in active.values()))
             engine.step(n)
+            fences.append(engine.fence())
+            while len(fences) > ahead:
+                engine.wait(fences.popleft())
             lups += n * sum(a[2].workload.nodes for a in active.values())
             for rid in list(active):
                 a = active[rid]
@@ -189,6 +205,16 @@ class GpuBatchEngine(Engine):
 
     def fields(self, token):
         return token[3]
+
+    def fence(self):
+        import torch
+
+        ev = torch.cuda.Event()
+        ev.record(self.stream)
+        return ev
+
+    def wait(self, fence) -> None:
+        fence.synchronize()
 
 
 def serve_plain(requests: List[Request], storage: str = "f32", device=None,

@@ -111,3 +111,41 @@ def test_oversize_request_is_refused():
     reqs = small_stream(n=3)
     with pytest.raises(ValueError):
         serve(reqs, eng, 1.0, clock=clock, sleep=clock.sleep)
+
+
+class QueueingFakeEngine(FakeEngine):
+    """Steps are only enqueued; the device catches up when the host waits on a fence."""
+
+    def __init__(self, clock):
+        super().__init__(clock)
+        self.enqueued = 0
+        self.completed = 0
+        self.max_in_flight = 0
+
+    def step(self, n):
+        for rid in self.active:
+            self.steps_done[rid] += n
+        self.enqueued += 1
+        self.max_in_flight = max(self.max_in_flight, self.enqueued - self.completed)
+
+    def fence(self):
+        return self.enqueued
+
+    def wait(self, fence):
+        if fence > self.completed:
+            self.clock.t += (fence - self.completed) * 1e-4
+            self.completed = fence
+
+
+@pytest.mark.parametrize("ahead", [1, 2, 4])
+def test_host_runs_a_bounded_number_of_chunks_ahead(ahead):
+    clock = FakeClock()
+    eng = QueueingFakeEngine(clock)
+    reqs = small_stream(n=40, rate=2000.0)
+    stats = serve(reqs, eng, 1e18, chunk=16, clock=clock, sleep=clock.sleep, ahead=ahead)
+    assert len(stats.results) == len(reqs)
+    for r in reqs:
+        assert eng.steps_done[r.rid] == r.workload.steps
+    # after each chunk the host waits until at most `ahead` chunks are queued
+    assert eng.max_in_flight == ahead + 1
+    assert eng.enqueued - eng.completed <= ahead
