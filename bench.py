@@ -31,21 +31,28 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-BYTES_PER_VALUE = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+BYTES_PER_VALUE = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "f16s": 2, "bf16s": 2}
 POPS = 13  # 9 D2Q9 + 4 D2Q4 populations, each read once and written once per update
+SPLIT_MOMENT_BYTES = 3 * 4  # moment-split storage: j_x, j_r, T - T0 in FP32 per node
+
+
+def bytes_per_node(storage: str) -> int:
+    """Bytes of one node's stored state: 13 populations, plus the FP32 moments of moment-split storage."""
+    return POPS * BYTES_PER_VALUE[storage] + (SPLIT_MOMENT_BYTES if storage.endswith("s") else 0)
 
 
 def bytes_per_lup(storage: str) -> int:
-    """Algorithmic DRAM bytes per lattice update, either pattern: every population read
+    """Algorithmic DRAM bytes per lattice update, either pattern: every node's stored state read
     once and written once (the AA pattern's edge moments are a few per cent more and are
     not counted)."""
-    return POPS * 2 * BYTES_PER_VALUE[storage]
+    return 2 * bytes_per_node(storage)
 
 
 def resident_mb(storage: str, pattern: str, nodes: int) -> float:
     """Population storage of the lattices (one buffer for the AA pattern, two otherwise), in MB."""
-    return POPS * BYTES_PER_VALUE[storage] * (1 if pattern == "aa" else 2) * nodes / 1e6
+    return bytes_per_node(storage) * (1 if pattern == "aa" else 2) * nodes / 1e6
 METRIC = "MLUPS & HBM-roofline % (D2Q9+D2Q4 LES); serving p50/p99 latency vs plain"
+HOLD_CYCLES = 4_000_000  # device-side hold before a timed region: about 2 ms at 2 GHz
 KERNEL_SRC = os.path.join(ROOT, "paper_1002_3028_gb300", "csrc", "lbm_kernels.cuh")
 AA_SRC = os.path.join(ROOT, "paper_1002_3028_gb300", "csrc", "lbm_aa.cuh")
 
@@ -353,16 +360,28 @@ def run_gpu(args):
         replicas.barrier()
         torch.cuda.synchronize(device)
 
-    # warm-up, then the device-timed region: K steps bracketed by events on the launching stream
+    # The error check against the FP64 path runs before the timed region: it is untimed work
+    # that also brings the GPU to its working clocks before the region starts.
+    errors = error_vs_f64(works, args.storage, device, pattern=args.pattern)
+
+    # The clock sampler runs from before the warm-up to after the timed region, so that its
+    # first nvidia-smi process is not started inside the timed region.  Warm-up, then the
+    # device-timed region: K steps bracketed by events on the launching stream.  Before the
+    # start event the stream is held on the device for about 2 ms (a sleep kernel, outside the
+    # region), so the start event and the steps are already enqueued when the GPU reaches
+    # them: the region holds the device work of the K steps, not the host's launch latency.
+    clk = ClockSampler(local).__enter__()
     step(args.warmup)
     barrier()
+    time.sleep(0.3)  # the sampler's first reading lands before the region
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        ev0.record(stream)
-        step(args.steps)
-        ev1.record(stream)
-        ev1.synchronize()
+    torch.cuda._sleep(HOLD_CYCLES)
+    ev0.record(stream)
+    step(args.steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    clk.__exit__(None, None, None)
     barrier()
     ms, units = replicas.combine(ev0.elapsed_time(ev1), nodes * args.steps, device)
     mlups = units / (ms * 1e-3) / 1e6
@@ -373,43 +392,41 @@ def run_gpu(args):
     finite = all(bool(torch.isfinite(lat.fields(dtype=torch.float32)).all().item()) for lat in lats)
     flags = max(lat.check() for lat in lats)
 
-    # end to end through the public API: every lattice's initial state from pinned host
-    # memory, K steps, every lattice's fields back to pinned host memory, all timed
+    # end to end through the public API: every lattice's initial state (its checkpoint in the
+    # storage type, lbm_save's layout) from pinned host memory through lbm_restore, K steps,
+    # every lattice's fields back to pinned host memory, all timed
     host_states, dev_states, outs = [], [], []
     for lat in lats:
-        fd, gd = lat.get_state()
-        fh = torch.empty(fd.shape, dtype=torch.float64).pin_memory()
-        gh = torch.empty(gd.shape, dtype=torch.float64).pin_memory()
-        fh.copy_(fd)
-        gh.copy_(gd)
-        host_states.append((fh, gh))
-        dev_states.append((torch.empty_like(fd), torch.empty_like(gd)))
+        planes, _ = lat.save()
+        ph = torch.empty(planes.shape, dtype=planes.dtype).pin_memory()
+        ph.copy_(planes)
+        host_states.append(ph)
+        dev_states.append(torch.empty_like(planes))
         outs.append((torch.empty((4, lat.nr, lat.nx), dtype=torch.float32, device=device),
                      torch.empty((4, lat.nr, lat.nx), dtype=torch.float32).pin_memory()))
-        del fd, gd
+        del planes
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for lat, (fh, gh), (fd, gd) in zip(lats, host_states, dev_states):
-        fd.copy_(fh, non_blocking=True)
-        gd.copy_(gh, non_blocking=True)
-        lat.set_state(fd, gd, lat.step_count, stream=stream)
+    for lat, ph, pd in zip(lats, host_states, dev_states):
+        pd.copy_(ph, non_blocking=True)
+        lat.restore_async(pd, lat.step_count, stream=stream)
     step(args.steps, stream=stream)
     for lat, (od, oh) in zip(lats, outs):
-        lat.fields(out=od)
+        lat.fields(out=od, stream=stream)
         oh.copy_(od, non_blocking=True)
     e1.record(stream)
     e1.synchronize()
     barrier()
     e2e_ms, e2e_units = replicas.combine(e0.elapsed_time(e1), nodes * args.steps, device)
-    h2d = sum((fh.numel() + gh.numel()) * 8 for fh, gh in host_states)
+    h2d = sum(ph.numel() * ph.element_size() for ph in host_states)
     d2h = sum(oh.numel() * 4 for _, oh in outs)
     e2e = {"value": e2e_units / (e2e_ms * 1e-3) / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-           "note": "initial states uploaded, K steps, fields downloaded; copies amortised over K"}
+           "note": "initial states (storage-type checkpoints) uploaded and restored, K steps, fields "
+                   "downloaded; copies amortised over K"}
 
-    errors = error_vs_f64(works, args.storage, device, pattern=args.pattern)
     if rank != 0:
         replicas.finish()
         return 0
@@ -443,53 +460,283 @@ def run_gpu(args):
         "fields_finite": finite,
         "device_flags": flags,
     }
+    if ws == 1 and not args.no_extras and len(lats) == 1:
+        # the metric's other halves: the batched ensemble and the serving loop (after the headline
+        # measurement, so they do not touch it)
+        for lat in lats:
+            lat.close()
+        torch.cuda.empty_cache()
+        line["ensemble"] = {st: ensemble_object(device, st) for st in ("f16s", "f16")}
+        line["serving"] = serving_object(device, args.requests, args.rate, args.budget_gb, args.chunk,
+                                         storage=args.serve_storage)
     print(json.dumps(line), flush=True)
     replicas.finish()
     return 0
 
 
-def run_serving(args):
-    """Continuous-batching service (FP16 batch) against the plain FP32 one-at-a-time path."""
+def field_errors(Fa, Fb) -> dict:
+    """Largest relative differences of fields Fa from Fb ((4, nr, nx): rho, u_x, u_r, T): rho and T
+    against their own maxima, u against the maximum speed."""
+    speed = float(Fb[1:3].abs().max())
+    return {"rho": float((Fa[0] - Fb[0]).abs().max() / Fb[0].abs().max()),
+            "u": float((Fa[1:3] - Fb[1:3]).abs().max()) / max(speed, 1e-30),
+            "T": float((Fa[3] - Fb[3]).abs().max() / Fb[3].abs().max())}
+
+
+def storage_errors(w, storage: str, steps: int, device) -> dict:
+    """Errors of a storage type against the FP64 path on one workload (untimed):
+
+    - ``per_step``: after `steps` steps in `storage`, its state is copied exactly (as FP64) into
+      an FP64 lattice and both take one more step; the fields are compared.  This is the bound
+      that holds at any time, turbulent or not;
+    - ``after_steps``: `storage`, FP32 and FP64 run `steps` steps from rest; the `storage` and
+      FP32 fields are compared with the FP64 ones.  On a turbulent jet the trajectories diverge
+      whatever the precision, which the FP32 column shows.
+    """
+    from paper_1002_3028_gb300 import lbm
+
+    a = lbm.Lattice.from_workload(w, storage, device=device)
+    b = lbm.Lattice.from_workload(w, "f64", device=device)
+    a.step(steps)
+    b.step(steps)
+    out = {"steps": steps, "after_steps": {storage: field_errors(a.fields(), b.fields())}}
+    if storage != "f32":
+        c = lbm.Lattice.from_workload(w, "f32", device=device)
+        c.step(steps)
+        out["after_steps"]["f32"] = field_errors(c.fields(), b.fields())
+        c.close()
+    f, g = a.get_state()
+    b.set_state(f, g, a.step_count)
+    a.step(1)
+    b.step(1)
+    out["per_step"] = field_errors(a.fields(), b.fields())
+    a.close()
+    b.close()
+    return out
+
+
+def worst(errs, key) -> dict:
+    """Component-wise maximum of the `key` error dicts of a list of storage_errors results."""
+    out = {}
+    for e in errs:
+        d = e
+        for k in key.split("."):
+            d = d[k]
+        for c, v in d.items():
+            out[c] = max(out.get(c, 0.0), v)
+    return out
+
+
+def ensemble_object(device, storage: str = "f16s", steps: int = 5000, warm: int = 64, count: int = 256) -> dict:
+    """The ragged ensemble (256 jets, 2-byte storage, one batch, persistent launches from a captured
+    CUDA graph), timed over `steps` steps of every member, with its roofline and errors."""
     import torch
 
     from paper_1002_3028_gb300 import inputs as I
     from paper_1002_3028_gb300 import lbm
+
+    works = I.ensemble_workloads(count, seed=7)
+    nodes = sum(w.nodes for w in works)
+    lats = [lbm.Lattice.from_workload(w, storage, device=device) for w in works]
+    batch = lbm.Batch(storage)
+    for lat in lats:
+        batch.add(lat)
+    stream = torch.cuda.current_stream(device)
+    batch.step(warm, graph=True, stream=stream)
+    torch.cuda.synchronize(device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda._sleep(HOLD_CYCLES)
+    e0.record(stream)
+    batch.step(steps, graph=True, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    sec = e0.elapsed_time(e1) * 1e-3
+    launch = batch.launch()
+    flags = max(lat.check() for lat in lats)
+    batch.close()
+    for lat in lats:
+        lat.close()
+    del lats
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_per_lup(storage) * nodes * steps / sec / 1e9
+    picks = [works[k] for k in range(0, count, count // 4)][:4]
+    errs = [storage_errors(w, storage, 1000, device) for w in picks]
+    return {"workload": f"{count} ragged jets, seed 7 ({nodes} nodes)", "storage": storage, "steps": steps,
+            "glups": nodes * steps / sec / 1e9, "ms_per_step": sec * 1e3 / steps,
+            "launch": dict(zip(("band_rows", "warps_per_cta", "tiles"), launch)),
+            "graph": "one captured launch of 64 steps, replayed",
+            "roofline": {"bound": "hbm", "bytes_per_lup": bytes_per_lup(storage), "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind},
+            "error_vs_f64": {"lattices": len(picks), "per_step": worst(errs, "per_step"),
+                             "after_1000_steps": {k: worst(errs, "after_steps." + k)
+                                                  for k in errs[0]["after_steps"]}},
+            "device_flags": flags}
+
+
+def plain_service_times(reqs, storage: str, device, n1: int = 100, n2: int = 500):
+    """Service time of every request on the plain path (one lattice alone, created, stepped in
+    one persistent launch, fields read back), measured request by request: creation and read-back
+    with the host clock, and the launch time for the request's step count from two timed launches
+    of n1 and n2 steps (a persistent launch costs a + b n; both launches are measured)."""
+    import torch
+
+    from paper_1002_3028_gb300 import lbm
+
+    out = []
+    for req in reqs:
+        w = req.workload
+        t0 = time.perf_counter()
+        lat = lbm.Lattice.from_workload(w, storage, device=device)
+        torch.cuda.synchronize(device)
+        t_create = time.perf_counter() - t0
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        lat.step(n1)
+        ev[1].record()
+        lat.step(n2)
+        ev[2].record()
+        ev[2].synchronize()
+        ta, tb = ev[0].elapsed_time(ev[1]) * 1e-3, ev[1].elapsed_time(ev[2]) * 1e-3
+        slope = (tb - ta) / (n2 - n1)
+        icpt = ta - slope * n1
+        t0 = time.perf_counter()
+        lat.fields(dtype=torch.float32).cpu()
+        t_fields = time.perf_counter() - t0
+        lat.close()
+        out.append(t_create + icpt + slope * w.steps + t_fields)
+    return out
+
+
+def fifo_replay(reqs, service):
+    """One server, first come first served: finish_i = max(arrival_i, finish_(i-1)) + service_i."""
+    from paper_1002_3028_gb300.serve import Result, ServeStats
+
+    t = 0.0
+    results = []
+    for req, s in zip(sorted(reqs, key=lambda r: r.arrival_s), service):
+        start = max(req.arrival_s, t)
+        t = start + s
+        results.append(Result(req.rid, req.arrival_s, start, t, req.workload.steps, req.workload.nodes))
+    return ServeStats(results, t, float(sum(r.workload.nodes * r.workload.steps for r in reqs)))
+
+
+def serving_object(device, count: int = 2000, rate: float = 40.0, budget_gb: float = 120.0, chunk: int = 256,
+                   pattern: str = "ab", validate: int = 30, storage: str = "f16s") -> dict:
+    """The serving workload: `count` Poisson requests at `rate`/s, jets drawn like the ensemble with
+    1000-20000 steps, admitted by an HBM budget into one batch of 2-byte storage (FP16 moment-split
+    by default: within 1e-3 of FP64 over whole requests; continuous batching), against the plain
+    FP32 path that runs one request at a time."""
+    import torch
+
+    from paper_1002_3028_gb300 import inputs as I
     from paper_1002_3028_gb300.serve import GpuBatchEngine, serve, serve_plain
+
+    reqs = I.request_stream(count=count, rate_per_s=rate, seed=11)
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    batched = serve(reqs, GpuBatchEngine(storage, device=device, pattern=pattern), budget_gb * 1e9, chunk=chunk)
+    torch.cuda.synchronize(device)
+    batched_wall = time.perf_counter() - t0
+    # the plain path: every request's service time measured alone, then queued first come first
+    # served; the first `validate` requests are also served for real to check the replay
+    service = plain_service_times(reqs, "f32", device)
+    plain = fifo_replay(reqs, service)
+    sub = sorted(reqs, key=lambda r: r.arrival_s)[:validate]
+    real = serve_plain(sub, "f32", device=device)
+    model = fifo_replay(sub, service[:validate])
+    picks = [reqs[r.rid].workload for r in batched.results[:: max(1, len(reqs) // 4)][:4]]
+    errs = [storage_errors(w, storage, w.steps, device) for w in picks]
+    b, p_ = batched.summary(), plain.summary()
+    return {"workload": f"{count} Poisson requests at {rate}/s, jets drawn like the ensemble, "
+                        f"steps U{{1000..20000}}, seed 11", "budget_gb": budget_gb, "chunk_steps": chunk,
+            "batched": {**b, "storage": storage, "wall_s": batched_wall, "pattern": pattern},
+            "plain_f32_one_at_a_time": {**p_, "how": "each request's service time measured alone (creation, "
+                                        "launches of 100 and 500 steps, fields read back), queued first come "
+                                        "first served",
+                                        "replay_check": {"requests": validate, "real_makespan_s": real.makespan_s,
+                                                         "replayed_makespan_s": model.makespan_s}},
+            "mlups_ratio_batched_over_plain": b["mlups"] / p_["mlups"],
+            "error_vs_f64_sample": {"requests": [w.name for w in picks], "storage": storage,
+                                        "per_step": worst(errs, "per_step"),
+                                        "after_request_steps": {k: worst(errs, "after_steps." + k)
+                                                                for k in errs[0]["after_steps"]}}}
+
+
+def l2_errors(Fa, Fb) -> dict:
+    """Relative L2 differences of fields Fa from Fb: ||a - b|| / ||b|| over the lattice, for rho, for
+    the velocity vector (u_x, u_r) and for T."""
+    def rel(a, b):
+        return float(((a - b) ** 2).sum().sqrt() / (b ** 2).sum().sqrt())
+
+    return {"rho": rel(Fa[0], Fb[0]), "u": rel(Fa[1:3], Fb[1:3]), "T": rel(Fa[3], Fb[3])}
+
+
+def run_sweep(args):
+    """The precision sweep: the 4096 x 1024 jet stored in FP32, FP16 and BF16 against an FP64 GPU
+    run of the same steps (relative L2 and max errors of rho, u, T), with the MLUPS of each storage
+    type (K timed steps in one persistent launch after W warm-up steps)."""
+    import torch
+
+    from paper_1002_3028_gb300 import lbm
 
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    reqs = I.request_stream(count=args.requests, rate_per_s=args.rate, seed=11)
-    torch.cuda.synchronize()
+    device = torch.device("cuda", 0)
+    w = workloads_by_name(args.workload if args.workload != "sweep" else "jet4096x1024")[0]
+    ref = lbm.Lattice.from_workload(w, "f64", device=device)
+    ref.step(args.sweep_steps)
+    Fr = ref.fields()
+    ref.close()
+    rows = {}
+    for storage in ("f32", "f16s", "bf16s", "f16", "bf16"):
+        a = lbm.Lattice.from_workload(w, storage, device=device)
+        a.step(args.sweep_steps)
+        Fa = a.fields()
+        rows[storage] = {"l2": l2_errors(Fa, Fr), "max": field_errors(Fa, Fr)}
+        del Fa
+        a.step(args.warmup)
+        torch.cuda.synchronize(device)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda._sleep(HOLD_CYCLES)
+        e0.record()
+        a.step(args.steps)
+        e1.record()
+        e1.synchronize()
+        rows[storage]["mlups"] = w.nodes * args.steps / (e0.elapsed_time(e1) * 1e-3) / 1e6
+        rows[storage]["bytes_per_lup"] = bytes_per_lup(storage)
+        a.close()
+    line = {"metric": METRIC, "value": rows["f16s"]["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"precision sweep: jet {w.cfg.nx}x{w.cfg.nr}, {args.sweep_steps} steps from "
+                                   "rest against the FP64 GPU path",
+                       "storage": "f32; f16s, bf16s (moment-split); f16, bf16 (rest deviations)"},
+            "sweep": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serving(args):
+    """The serving workload alone (one JSON line)."""
+    import torch
+
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    device = torch.device("cuda", 0)
     with ClockSampler(0) as clk:
-        batched = serve(reqs, GpuBatchEngine("f16", pattern=args.pattern), args.budget_gb * 1e9, chunk=args.chunk,
-                        keep_fields=True)
-    torch.cuda.synchronize()
-    plain = serve_plain(reqs, "f32")
-    # error of the served FP16 fields against an FP64 run of the same request, on a sample
-    errs = []
-    for res in batched.results[:: max(1, len(reqs) // 4)][:4]:
-        w = reqs[res.rid].workload
-        ref = lbm.Lattice.from_workload(w, "f64")
-        ref.step(w.steps)
-        F = ref.fields().cpu().numpy()
-        G = res.fields.double().numpy()
-        speed = max(float(abs(F[1]).max()), float(abs(F[2]).max()))
-        errs.append({"rid": res.rid, "u": float(abs(G[1:3] - F[1:3]).max() / speed),
-                     "T": float(abs(G[3] - F[3]).max() / abs(F[3]).max())})
-        ref.close()
-    b, p_ = batched.summary(), plain.summary()
+        srv = serving_object(device, args.requests, args.rate, args.budget_gb, args.chunk, args.pattern,
+                             storage=args.serve_storage)
+    b = srv["batched"]
     line = {
         "metric": METRIC, "value": b["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": None, "warmup": 0,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": f"serving: {len(reqs)} Poisson requests at {args.rate}/s, jets drawn like the "
-                               f"ensemble, steps U{{1000..20000}}, seed 11", "storage": "f16 (batched), f32 (plain)",
-                   "pattern": args.pattern + " (batched)", "budget_gb": args.budget_gb, "chunk_steps": args.chunk},
-        "serving": {"batched_f16": b, "plain_f32_one_at_a_time": p_,
-                    "mlups_ratio_batched_over_plain": b["mlups"] / p_["mlups"],
-                    "f16_error_vs_f64_sample": errs},
-        "clocks": clk.summary(),
+        "data": "synthetic", "config": {"workload": "serving: " + srv["workload"],
+                                        "storage": srv["batched"]["storage"] + " (batched), f32 (plain)"},
+        "serving": srv, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -512,10 +759,16 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="tune the launch shape before timing")
-    ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
+    ap.add_argument("--sweep-steps", type=int, default=1000,
+                    help="precision sweep (--workload sweep): steps from rest compared with FP64")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the ensemble and serving objects of the default line")
     ap.add_argument("--rate", type=float, default=40.0, help="serving: arrivals per second")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: device memory budget")
     ap.add_argument("--chunk", type=int, default=256, help="serving: most steps per batch launch sequence")
+    ap.add_argument("--serve-storage", default="f16s", choices=["f16s", "bf16s", "f16", "bf16", "f32"],
+                    help="serving: storage type of the batched lattices")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -523,6 +776,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_gpu(args)
 
 

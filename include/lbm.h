@@ -65,9 +65,21 @@ typedef enum {
 } lbm_status;
 
 /* storage type of the populations on the device (the arithmetic is FP64
- * for LBM_F64 and FP32 for the others).  All types store the deviation
- * from the rest state, f_k - w_k rho0 and g_k - T0/4. */
-typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3 } lbm_storage;
+ * for LBM_F64 and FP32 for the others).
+ *   LBM_F64, LBM_F32, LBM_F16, LBM_BF16  every population stored as its
+ *       deviation from the rest state, f_k - w_k rho0 and g_k - T0/4
+ *       (the reduced-precision format of the populations of Eq. 1 as
+ *       deviations from the rest weights).
+ *   LBM_F16S, LBM_BF16S  moment-split storage: per node the moments
+ *       j = rho u and T - T0 in FP32, and each population as a 2-byte
+ *       deviation from the part of its equilibrium linear in those moments,
+ *       f_k - w_k rho0 - 3 w_k e_k.j and g_k - T/4 - T e_k.j / (2 rho0).  The
+ *       2-byte rounding then scales with the non-equilibrium and quadratic
+ *       parts, not with the velocity or the temperature excess: 76 bytes per
+ *       lattice update instead of 52.  Two-buffer pattern only.  A checkpoint
+ *       (lbm_save) holds the 13 population planes, then the three moment
+ *       planes (j_x, j_r, T - T0) in FP32. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3, LBM_F16S = 4, LBM_BF16S = 5 } lbm_storage;
 
 typedef enum { LBM_IN_INLET = 0, LBM_IN_PERIODIC = 1 } lbm_bc_in;
 typedef enum { LBM_OUT_OUTFLOW = 0, LBM_OUT_WALL = 1, LBM_OUT_PERIODIC = 2 } lbm_bc_out;

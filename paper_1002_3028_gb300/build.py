@@ -27,7 +27,8 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompil
 
 # The FP32-arithmetic kernels (FP32/FP16/BF16 storage) use the hardware
 # reciprocal and square-root approximations; the FP64 kernels stay IEEE.
-FLOAT_TUS = ("lbm_step_f32.cu", "lbm_step_f16.cu", "lbm_step_bf16.cu")
+FLOAT_TUS = ("lbm_step_f32.cu", "lbm_step_f16.cu", "lbm_step_bf16.cu", "lbm_step_f16s.cu", "lbm_step_bf16s.cu",
+             "lbm_noalloc.cu")
 FLOAT_FLAGS = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
 
 

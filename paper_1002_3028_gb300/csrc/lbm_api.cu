@@ -117,6 +117,9 @@ constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
+// moment-split storage: FP32 moment planes beside the 2-byte population planes
+bool is_split(int storage) { return storage == LBM_F16S || storage == LBM_BF16S; }
+
 // lattice columns per warp strip of the step kernel: 32 nodes per lane-slot,
 // two per lane in FP32 arithmetic
 int strip_cols(int storage) { return storage == LBM_F64 ? 32 : 64; }
@@ -127,6 +130,8 @@ size_t storage_bytes(int storage)
     case LBM_F64: return 8;
     case LBM_F32: return 4;
     case LBM_F16: return 2;
+    case LBM_F16S: return 2;
+    case LBM_BF16S: return 2;
     case LBM_BF16: return 2;
     default: return 0;
     }
@@ -170,6 +175,8 @@ int check_desc(const lbm_desc *d)
         return fail(LBM_ERR_INVALID_ARG, "lattice %d x %d exceeds 13 * (nr + 2) * pitch < 2^31 elements", d->nx, d->nr);
     if (d->pattern != LBM_PATTERN_AB && d->pattern != LBM_PATTERN_AA)
         return fail(LBM_ERR_INVALID_ARG, "unknown pattern %d", d->pattern);
+    if (d->pattern == LBM_PATTERN_AA && is_split(d->storage))
+        return fail(LBM_ERR_INVALID_ARG, "moment-split storage (LBM_F16S, LBM_BF16S) has the two-buffer pattern only");
     if (d->bc_in < 0 || d->bc_in > 1 || d->bc_out < 0 || d->bc_out > 2 || d->bc_top < 0 || d->bc_top > 1 ||
         d->bc_bottom < 0 || d->bc_bottom > 1)
         return fail(LBM_ERR_INVALID_ARG, "unknown boundary kind");
@@ -189,7 +196,9 @@ Layout make_layout(const lbm_desc *d)
     Layout L;
     L.pitch = row_pitch(d->nx);
     L.plane = (int64_t)L.pitch * (d->nr + 2);  // ghost rows -1 and nr
-    L.buf_bytes = align_up((size_t)13 * (size_t)L.plane * storage_bytes(d->storage));
+    L.buf_bytes = is_split(d->storage)
+                      ? align_up((size_t)lbm::split_moff(L.plane) + (size_t)lbm::SPLIT_MOMENTS * (size_t)L.plane * 4)
+                      : align_up((size_t)13 * (size_t)L.plane * storage_bytes(d->storage));
     const bool aa = d->pattern == LBM_PATTERN_AA;
     size_t o = 0;
     L.off_buf[0] = o;
@@ -307,6 +316,7 @@ lbm::StepParams<C> make_params(const lbm_lattice *h, const C *u_in, const C *T_i
     p.dT_out = C(d.T_out - d.T0);
     p.T_lo = C(h->T_lo);
     p.tab_scale = h->ntab > 1 ? C((double)(h->ntab - 1) / (h->T_hi - h->T_lo)) : C(0);
+    p.hir0 = C(0.5 / d.rho0);
     p.u_in = u_in;
     p.T_in = T_in;
     p.nu_tab = nu;
@@ -337,10 +347,13 @@ int item_group(const lbm_lattice *h) { return h->group > 0 ? h->group : 1; }
 // default) working through strip x band tiles.  A tile of step t + 1 waits
 // for the tiles around it of step t, which precede it by one step's worth
 // of tiles in the work order; the automatic band height keeps that distance
-// at about 4.5 rounds of the resident warps (3.4 for 2-byte storage), which
+// at about 5.4 rounds of the resident warps (3.4 for 2-byte storage), which
 // leaves the waits rare, with bands of 1..8 rows (each band stages two halo
-// rows).  On the 4096 x 1024 jet this picks band 6 for FP32 and band 8 for
-// FP16 storage, the fastest of bands 4..10 measured for each.  Lattices
+// rows).  On the 4096 x 1024 jet this picks band 5 for FP32 and band 8 for
+// FP16 storage.  FP32 at band 6 (4.5 rounds) ran either at 79 or at 87 us
+// per step, one or the other for a whole launch, with three to four times
+// as many blocked waits and 3% more DRAM reads in the slow launches; at
+// band 5 every launch ran at 80 us (band 4: 83).  Lattices
 // with fewer tiles than that are bound by the latency of one tile per step
 // and get the shortest bands (1024 x 256: band 1, 2.3x faster than band 4).
 // The grid holds at most one step's worth of tiles: warps beyond that could
@@ -353,6 +366,8 @@ int plan_launch(lbm_lattice *h)
     case LBM_F64: e = h->aa ? lbm::occupancy_aa_run_f64(h->warps, &per_sm) : lbm::occupancy_run_f64(h->warps, &per_sm); break;
     case LBM_F32: e = h->aa ? lbm::occupancy_aa_run_f32(h->warps, &per_sm) : lbm::occupancy_run_f32(h->warps, &per_sm); break;
     case LBM_F16: e = h->aa ? lbm::occupancy_aa_run_f16(h->warps, &per_sm) : lbm::occupancy_run_f16(h->warps, &per_sm); break;
+    case LBM_F16S: e = lbm::occupancy_run_f16s(h->warps, &per_sm); break;
+    case LBM_BF16S: e = lbm::occupancy_run_bf16s(h->warps, &per_sm); break;
     default: e = h->aa ? lbm::occupancy_aa_run_bf16(h->warps, &per_sm) : lbm::occupancy_run_bf16(h->warps, &per_sm); break;
     }
     if (e != cudaSuccess)
@@ -366,7 +381,7 @@ int plan_launch(lbm_lattice *h)
     } else {
         // tenths of a round (AA: 3.4 for every storage type; band 8 on the 4096 x 1024 jet,
         // the fastest of bands 4..16 measured for FP32 and FP16)
-        const int64_t rounds10 = storage_bytes(h->d.storage) == 2 || h->aa ? 34 : 45;
+        const int64_t rounds10 = storage_bytes(h->d.storage) == 2 || h->aa ? 34 : 54;
         const int64_t want_tiles = std::max<int64_t>(1, rounds10 * resident_warps / 10);
         const int64_t band = ((int64_t)h->d.nr * nstrips + want_tiles - 1) / want_tiles;
         h->band_eff = (int)std::min<int64_t>(8, std::max<int64_t>(1, band));
@@ -453,6 +468,18 @@ int fill_ghosts(lbm_lattice *h, cudaStream_t s)
         e = lbm::launch_fill_f16(p, s);
         break;
     }
+    case LBM_F16S: {
+        auto p = params_f(h);
+        p.dst = h->buf(h->cur);
+        e = lbm::launch_fill_f16s(p, s);
+        break;
+    }
+    case LBM_BF16S: {
+        auto p = params_f(h);
+        p.dst = h->buf(h->cur);
+        e = lbm::launch_fill_bf16s(p, s);
+        break;
+    }
     default: {
         auto p = params_f(h);
         p.dst = h->buf(h->cur);
@@ -517,6 +544,8 @@ int batch_occupancy(lbm_batch *b, int warps, int *per_sm)
     case LBM_F64: e = b->aa ? lbm::occupancy_aa_batch_f64(warps, per_sm) : lbm::occupancy_batch_f64(warps, per_sm); break;
     case LBM_F32: e = b->aa ? lbm::occupancy_aa_batch_f32(warps, per_sm) : lbm::occupancy_batch_f32(warps, per_sm); break;
     case LBM_F16: e = b->aa ? lbm::occupancy_aa_batch_f16(warps, per_sm) : lbm::occupancy_batch_f16(warps, per_sm); break;
+    case LBM_F16S: e = lbm::occupancy_batch_f16s(warps, per_sm); break;
+    case LBM_BF16S: e = lbm::occupancy_batch_bf16s(warps, per_sm); break;
     default: e = b->aa ? lbm::occupancy_aa_batch_bf16(warps, per_sm) : lbm::occupancy_batch_bf16(warps, per_sm); break;
     }
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "batch occupancy query");
@@ -681,6 +710,12 @@ cudaError_t batch_launch(lbm_batch *b, int nsteps, cudaStream_t s)
     case LBM_F16:
         return lbm::launch_batch_f16(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params), n,
                                      ctl, b->warps, ctas, b->far ? 1 : 0, s);
+    case LBM_F16S:
+        return lbm::launch_batch_f16s(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params), n,
+                                      ctl, b->warps, ctas, b->far ? 1 : 0, s);
+    case LBM_BF16S:
+        return lbm::launch_batch_bf16s(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params), n,
+                                       ctl, b->warps, ctas, b->far ? 1 : 0, s);
     default:
         return lbm::launch_batch_bf16(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params), n,
                                       ctl, b->warps, ctas, b->far ? 1 : 0, s);
@@ -1030,6 +1065,8 @@ static int step_impl(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
         case LBM_F64: e = lbm::launch_run_f64(params_d(h), ctl, h->warps, ctas, s); break;
         case LBM_F32: e = lbm::launch_run_f32(params_f(h), ctl, h->warps, ctas, s); break;
         case LBM_F16: e = lbm::launch_run_f16(params_f(h), ctl, h->warps, ctas, s); break;
+        case LBM_F16S: e = lbm::launch_run_f16s(params_f(h), ctl, h->warps, ctas, s); break;
+        case LBM_BF16S: e = lbm::launch_run_bf16s(params_f(h), ctl, h->warps, ctas, s); break;
         default: e = lbm::launch_run_bf16(params_f(h), ctl, h->warps, ctas, s); break;
         }
         if (e != cudaSuccess)
@@ -1116,6 +1153,8 @@ int lbm_selftest_wait_timeout(lbm_lattice *h, int32_t *flags)
         case LBM_F64: e = lbm::launch_run_f64(params_d(h), ctl, h->warps, ctas, s); break;
         case LBM_F32: e = lbm::launch_run_f32(params_f(h), ctl, h->warps, ctas, s); break;
         case LBM_F16: e = lbm::launch_run_f16(params_f(h), ctl, h->warps, ctas, s); break;
+        case LBM_F16S: e = lbm::launch_run_f16s(params_f(h), ctl, h->warps, ctas, s); break;
+        case LBM_BF16S: e = lbm::launch_run_bf16s(params_f(h), ctl, h->warps, ctas, s); break;
         default: e = lbm::launch_run_bf16(params_f(h), ctl, h->warps, ctas, s); break;
         }
     }
@@ -1152,6 +1191,8 @@ static int diagnostics_impl(lbm_lattice *h, lbm_diag *out, lbm_stream stream)
     case LBM_F64: e = lbm::launch_diag_f64(params_d(h), prev, partials, nblocks, res, s); break;
     case LBM_F32: e = lbm::launch_diag_f32(params_f(h), prev, partials, nblocks, res, s); break;
     case LBM_F16: e = lbm::launch_diag_f16(params_f(h), prev, partials, nblocks, res, s); break;
+    case LBM_F16S: e = lbm::launch_diag_f16s(params_f(h), prev, partials, nblocks, res, s); break;
+    case LBM_BF16S: e = lbm::launch_diag_bf16s(params_f(h), prev, partials, nblocks, res, s); break;
     default: e = lbm::launch_diag_bf16(params_f(h), prev, partials, nblocks, res, s); break;
     }
     double v[lbm::DIAG_SLOTS];
@@ -1191,6 +1232,8 @@ static int get_fields_impl(lbm_lattice *h, void *dev_out, int32_t out_type, lbm_
     case LBM_F64: e = lbm::launch_fields_f64(params_d(h), dev_out, f64, s); break;
     case LBM_F32: e = lbm::launch_fields_f32(params_f(h), dev_out, f64, s); break;
     case LBM_F16: e = lbm::launch_fields_f16(params_f(h), dev_out, f64, s); break;
+    case LBM_F16S: e = lbm::launch_fields_f16s(params_f(h), dev_out, f64, s); break;
+    case LBM_BF16S: e = lbm::launch_fields_bf16s(params_f(h), dev_out, f64, s); break;
     default: e = lbm::launch_fields_bf16(params_f(h), dev_out, f64, s); break;
     }
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "fields kernel launch");
@@ -1217,6 +1260,8 @@ static int get_state_impl(lbm_lattice *h, double *dev_f, double *dev_g, lbm_stre
     case LBM_F64: e = lbm::launch_state_out_f64(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
     case LBM_F32: e = lbm::launch_state_out_f32(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
     case LBM_F16: e = lbm::launch_state_out_f16(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+    case LBM_F16S: e = lbm::launch_state_out_f16s(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+    case LBM_BF16S: e = lbm::launch_state_out_bf16s(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
     default: e = lbm::launch_state_out_bf16(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
     }
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "state read kernel launch");
@@ -1243,6 +1288,8 @@ static int set_state_impl(lbm_lattice *h, const double *dev_f, const double *dev
         case LBM_F64: e = lbm::launch_state_in_f64(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
         case LBM_F32: e = lbm::launch_state_in_f32(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
         case LBM_F16: e = lbm::launch_state_in_f16(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+        case LBM_F16S: e = lbm::launch_state_in_f16s(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
+        case LBM_BF16S: e = lbm::launch_state_in_bf16s(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
         default: e = lbm::launch_state_in_bf16(b, dev_f, dev_g, d.nx, d.nr, h->L.pitch, h->L.plane, d.rho0, d.T0, s); break;
         }
     }
@@ -1260,6 +1307,8 @@ int lbm_checkpoint_bytes(const lbm_lattice *h, size_t *bytes)
     if (!valid(h) || !bytes)
         return fail(LBM_ERR_INVALID_ARG, "bad handle or NULL output");
     *bytes = (size_t)13 * (size_t)h->d.nr * (size_t)h->d.nx * storage_bytes(h->d.storage);
+    if (is_split(h->d.storage))  // then the FP32 moment planes
+        *bytes += (size_t)lbm::SPLIT_MOMENTS * (size_t)h->d.nr * (size_t)h->d.nx * 4;
     return LBM_OK;
 }
 
@@ -1284,6 +1333,19 @@ static int copy_planes(lbm_lattice *h, void *dense, bool out, cudaStream_t s)
                             : cudaMemcpy2DAsync(padded, pitch, flat, row, row, h->d.nr, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess)
             return cuda_fail(e, "checkpoint plane copy");
+    }
+    if (is_split(h->d.storage)) {  // the moment planes follow the 13 population planes
+        const size_t mrow = (size_t)h->d.nx * 4, mpitch = (size_t)h->L.pitch * 4;
+        char *mbase = buf + lbm::split_moff(h->L.plane);
+        char *mflat = static_cast<char *>(dense) + (size_t)13 * (size_t)h->d.nr * row;
+        for (int m = 0; m < lbm::SPLIT_MOMENTS; ++m) {
+            char *padded = mbase + ((size_t)m * (size_t)h->L.plane + (size_t)h->L.pitch + lbm::PAD_COLS) * 4;
+            char *flat = mflat + (size_t)m * (size_t)h->d.nr * mrow;
+            cudaError_t e = out ? cudaMemcpy2DAsync(flat, mrow, padded, mpitch, mrow, h->d.nr, cudaMemcpyDeviceToDevice, s)
+                                : cudaMemcpy2DAsync(padded, mpitch, flat, mrow, mrow, h->d.nr, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess)
+                return cuda_fail(e, "checkpoint moment plane copy");
+        }
     }
     return LBM_OK;
 }

@@ -96,6 +96,7 @@ struct alignas(16) StepParams {
     C inv_prt;        // 1 / Pr_t (Eq. 5)
     C dT_top, dT_bottom, dT_out;  // wall temperature minus T0
     C T_lo, tab_scale;            // table position s = (T - T_lo) * tab_scale
+    C hir0;                       // 1 / (2 rho0) (moment-split storage)
     const C *u_in, *T_in;         // inlet profiles, nr values
     const C *nu_tab, *al_tab;     // property tables, ntab values
     int *status;                  // error flags of the lattice
@@ -125,6 +126,105 @@ template <> __device__ __forceinline__ double store_as<double, double>(double v)
 template <> __device__ __forceinline__ float store_as<float, float>(float v) { return v; }
 template <> __device__ __forceinline__ __half store_as<__half, float>(float v) { return __float2half_rn(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 store_as<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
+
+// ---- moment-split storage of 2-byte types ------------------------------------
+// Storage types half_s and bf16_s keep, for every cell, the moments
+// j_x = rho u_x, j_r = rho u_r and T - T0 in three FP32 planes (after the 13
+// population planes of the buffer, at byte offset split_moff(plane)), and
+// each population as its 2-byte deviation d from the part of the equilibrium
+// that is linear in those moments:
+//   f_k - w_k rho0 = 3 w_k e_k.j + d_k,
+//   g_k - T0/4     = (T - T0)/4 + T e_k.j / (2 rho0) + d_k.
+// A node stores its own pre-collision moments and the deviations of its
+// post-collision populations from their linear parts at those moments; a
+// pull adds back the linear part at the moments stored with the pulled
+// value.  Both sides evaluate it with the same FP32 expression, so the only
+// loss is the 2-byte rounding of d, which holds the non-equilibrium and
+// quadratic parts only: its rounding no longer scales with the velocity or
+// the temperature excess of the jet.
+struct half_s {
+    __half v;
+};
+struct bf16_s {
+    __nv_bfloat16 v;
+};
+template <class S> struct IsSplit { static constexpr bool value = false; };
+template <> struct IsSplit<half_s> { static constexpr bool value = true; };
+template <> struct IsSplit<bf16_s> { static constexpr bool value = true; };
+constexpr int SPLIT_MOMENTS = 3;  // j_x, j_r, T - T0
+
+// byte offset of the first moment plane in a buffer of 13 planes of `plane` 2-byte values
+__host__ __device__ constexpr int64_t split_moff(int64_t plane) { return (13 * plane * 2 + 255) / 256 * 256; }
+
+template <> __device__ __forceinline__ float load_as<half_s, float>(const half_s *p) { return __half2float(__ldcg(&p->v)); }
+template <> __device__ __forceinline__ float load_as<bf16_s, float>(const bf16_s *p) { return __bfloat162float(__ldcg(&p->v)); }
+template <> __device__ __forceinline__ float load_as_shared<half_s, float>(const half_s *p) { return __half2float(p->v); }
+template <> __device__ __forceinline__ float load_as_shared<bf16_s, float>(const bf16_s *p) { return __bfloat162float(p->v); }
+template <> __device__ __forceinline__ half_s store_as<half_s, float>(float v) { return half_s{__float2half_rn(v)}; }
+template <> __device__ __forceinline__ bf16_s store_as<bf16_s, float>(float v) { return bf16_s{__float2bfloat16_rn(v)}; }
+
+template <class S>
+__device__ __forceinline__ float *split_m(S *buf, int64_t plane)
+{
+    return reinterpret_cast<float *>(reinterpret_cast<char *>(buf) + split_moff(plane));
+}
+template <class S>
+__device__ __forceinline__ const float *split_m(const S *buf, int64_t plane)
+{
+    return reinterpret_cast<const float *>(reinterpret_cast<const char *>(buf) + split_moff(plane));
+}
+
+// linear part of population q (deviation from rest) at moments (jx, jr, dT)
+// e.j for a lattice velocity e with components in {-1, 0, 1} (no product with a zero component)
+template <class C>
+__device__ __forceinline__ C edot(int ex, int ey, C jx, C jr)
+{
+    const C a = ex > 0 ? jx : -jx, b = ey > 0 ? jr : -jr;
+    return ex == 0 ? (ey == 0 ? C(0) : b) : (ey == 0 ? a : a + b);
+}
+
+template <class C>
+__device__ __forceinline__ C lin_part(const StepParams<C> &p, int q, C jx, C jr, C dT)
+{
+    if (q == 0)
+        return C(0);
+    if (q < 9)
+        return (C(3) * w9<C>(q)) * edot<C>(ex9(q), ey9(q), jx, jr);
+    return C(0.25) * dT + (p.T0 + dT) * p.hir0 * edot<C>(ex4(q - 9), ey4(q - 9), jx, jr);
+}
+
+// Moments a ghost cell (ci, cj) carries when node (i, j), with moments
+// (jx, jr, dT), writes it: the one node whose rule fills an axis, open-top,
+// inlet, outflow or periodic ghost cell writes its own moments there
+// (mirrored across the axis; the prescribed inflow at the inlet).  The
+// lattice corners and the cells beyond walls, which several nodes fill,
+// carry zero moments and their populations whole.  Returns false for those.
+template <class C>
+__device__ __forceinline__ bool ghost_moments(const StepParams<C> &p, int ci, int cj, C jx, C jr, C dT, C &gx, C &gr,
+                                              C &gT)
+{
+    const bool col_in = ci >= 0 && ci < p.nx, row_in = cj >= 0 && cj < p.nr;
+    gx = jx;
+    gr = jr;
+    gT = dT;
+    if (col_in && cj == -1) {
+        gr = -jr;
+        return p.bc_bottom == BOTTOM_AXIS;
+    }
+    if (col_in && cj == p.nr)
+        return p.bc_top == TOP_OPEN;
+    if (row_in && ci == -1) {
+        if (p.bc_in == IN_INLET) {
+            gx = p.rho0 * p.u_in[cj];
+            gr = C(0);
+            gT = p.T_in[cj] - p.T0;
+        }
+        return true;
+    }
+    if (row_in && ci == p.nx)
+        return p.bc_out != OUT_WALL;
+    return false;
+}
 
 template <class C>
 __device__ __forceinline__ int64_t cell(const StepParams<C> &p, int q, int i, int j)
@@ -371,6 +471,31 @@ template <class S, class C>
 __device__ __noinline__ void write_ghosts(const StepParams<C> &p, S *buf, int i, int j, int64_t t)
 {
     C fo[9], go[4];
+    if constexpr (IsSplit<S>::value) {
+        // the node's stored populations (its moments plus the stored deviations), then each
+        // ghost value as a deviation from the linear part at the ghost cell's own moments
+        float *M = split_m(buf, p.plane);
+        const int64_t o = cell(p, 0, i, j);
+        const C jx = M[o], jr = M[p.plane + o], dT = M[2 * p.plane + o];  // plain loads: this thread stored them
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            fo[k] = lin_part<C>(p, k, jx, jr, dT) + load_as_shared<S, C>(buf + cell(p, k, i, j));
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            go[k] = lin_part<C>(p, 9 + k, jx, jr, dT) + load_as_shared<S, C>(buf + cell(p, 9 + k, i, j));
+        ghost_rules<C>(p, fo, go, i, j, t, [&](int q, int ci, int cj, C v) {
+            C gx, gr, gT;
+            const int64_t oc = cell(p, 0, ci, cj);
+            if (ghost_moments<C>(p, ci, cj, jx, jr, dT, gx, gr, gT)) {
+                M[oc] = gx;
+                M[p.plane + oc] = gr;
+                M[2 * p.plane + oc] = gT;
+                v -= lin_part<C>(p, q, gx, gr, gT);
+            }
+            buf[cell(p, q, ci, cj)] = store_as<S, C>(v);
+        });
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 9; ++k)
         fo[k] = load_as_shared<S, C>(buf + cell(p, k, i, j));  // plain load: this thread stored it
@@ -392,15 +517,28 @@ __device__ __forceinline__ int64_t stream_cell(const StepParams<C> &p, int q, in
     return cell(p, p.aa ? opp_plane(q) : q, i - qex(q), j - qey(q));
 }
 
+// population q streamed into node (i, j) from a stored state (deviation from rest)
+template <class S, class C>
+__device__ __forceinline__ C pulled(const StepParams<C> &p, const S *src, int q, int i, int j)
+{
+    const int64_t c = stream_cell(p, q, i, j);
+    C v = load_as<S, C>(src + c);
+    if constexpr (IsSplit<S>::value) {  // plus the linear part at the source cell's moments
+        const float *M = split_m(src, p.plane) + (c - (int64_t)q * p.plane);
+        v += lin_part<C>(p, q, __ldcg(M), __ldcg(M + p.plane), __ldcg(M + 2 * p.plane));
+    }
+    return v;
+}
+
 template <class S, class C>
 __device__ __forceinline__ void pull(const StepParams<C> &p, const S *src, int i, int j, C (&f)[9], C (&g)[4])
 {
 #pragma unroll
     for (int k = 0; k < 9; ++k)
-        f[k] = load_as<S, C>(src + stream_cell(p, k, i, j));
+        f[k] = pulled<S, C>(p, src, k, i, j);
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-        g[k] = load_as<S, C>(src + stream_cell(p, 9 + k, i, j));
+        g[k] = pulled<S, C>(p, src, 9 + k, i, j);
 }
 
 template <class V>
@@ -468,6 +606,10 @@ __device__ __forceinline__ Mom<Vec<C, 1>> node_moments(const StepParams<C> &p, i
 template <class S, class C>
 __device__ __forceinline__ C jr_at(const StepParams<C> &p, const S *src, int i, int j)
 {
+    if constexpr (IsSplit<S>::value)
+        return (pulled<S, C>(p, src, 2, i, j) - pulled<S, C>(p, src, 4, i, j)) +
+               (pulled<S, C>(p, src, 5, i, j) - pulled<S, C>(p, src, 8, i, j)) +
+               (pulled<S, C>(p, src, 6, i, j) - pulled<S, C>(p, src, 7, i, j));
     return (ld<S, C>(p, src, 2, i, j - 1) - ld<S, C>(p, src, 4, i, j + 1)) +
            (ld<S, C>(p, src, 5, i - 1, j - 1) - ld<S, C>(p, src, 8, i - 1, j + 1)) +
            (ld<S, C>(p, src, 6, i + 1, j - 1) - ld<S, C>(p, src, 7, i + 1, j + 1));
@@ -771,35 +913,92 @@ __device__ __forceinline__ C sget(const S *stage, int q, int ex, int col)
     return load_as_shared<S, C>(stage + q * Wn::W + col + Wn::H - ex);
 }
 
+// Moment-split storage: the moment rows are staged too, each lattice row
+// once, into a per-warp ring of MSLOTS slots; a slot holds the three FP32
+// moment planes of one row over the strip's columns and MH columns on each
+// side.  A row's populations come from sources in rows r - 1, r and r + 1,
+// so the pull of row r reads three slots.
+template <int NV> struct MWin {
+    static constexpr int H = 4;                    // halo columns (one 16-byte chunk) on each side
+    static constexpr int W = 32 * NV + 2 * H;      // window length per moment plane
+    static constexpr int CH = W / 4;               // 16-byte chunks per moment plane
+    static constexpr int SLOT = SPLIT_MOMENTS * W;  // floats per slot
+};
+constexpr int MSLOTS = 5;  // moment rows r - 2 .. r + 2 around the row whose moments are formed
+
+// the staged moment windows of rows r - 1, r and r + 1 (null for other storage types)
+struct MRows {
+    const float *row[3];
+};
+
+// moment m (0: j_x, 1: j_r, 2: T - T0) of strip column col in row r - ey
+template <int NV>
+__device__ __forceinline__ float mget(const MRows &mr, int ey, int m, int col)
+{
+    return mr.row[1 - ey][m * MWin<NV>::W + col + MWin<NV>::H];
+}
+
+// start the copies of moment row r into a slot
+template <int NV, class C>
+__device__ __forceinline__ void issue_mrow(const StepParams<C> &p, const float *M, float *slot, int x0, int r, int lane)
+{
+    using MW = MWin<NV>;
+    const int row = (r + 1) * p.pitch + x0 - MW::H + PAD_COLS;
+#pragma unroll
+    for (int t0 = 0; t0 < SPLIT_MOMENTS * MW::CH; t0 += 32) {
+        const int t = t0 + lane;
+        if (t < SPLIT_MOMENTS * MW::CH) {
+            const int m = t / MW::CH, c = t - m * MW::CH;
+            cp_async16(slot + m * MW::W + 4 * c, M + (unsigned)(m * (int)p.plane + row + 4 * c));
+        }
+    }
+}
+
+// population q of strip column col, pulled from the stage (plus its linear part for
+// moment-split storage)
 template <class S, int NV, class C>
-__device__ __forceinline__ void stage_pops(const S *stage, int lane, Vec<C, NV> (&f)[9], Vec<C, NV> (&g)[4])
+__device__ __forceinline__ C spop(const StepParams<C> &p, const S *stage, const MRows &mr, int q, int col)
+{
+    const int ex = qex(q), ey = qey(q);
+    C v = sget<S, NV, C>(stage, q, ex, col);
+    if constexpr (IsSplit<S>::value) {
+        const int sc = col - ex;
+        v += lin_part<C>(p, q, mget<NV>(mr, ey, 0, sc), mget<NV>(mr, ey, 1, sc), q < 9 ? C(0) : mget<NV>(mr, ey, 2, sc));
+    }
+    return v;
+}
+
+template <class S, int NV, class C>
+__device__ __forceinline__ void stage_pops(const StepParams<C> &p, const S *stage, const MRows &mr, int lane,
+                                           Vec<C, NV> (&f)[9], Vec<C, NV> (&g)[4])
 {
 #pragma unroll
     for (int c = 0; c < NV; ++c) {
 #pragma unroll
         for (int k = 0; k < 9; ++k)
-            f[k].set(c, sget<S, NV, C>(stage, k, ex9(k), lane + 32 * c));
+            f[k].set(c, spop<S, NV, C>(p, stage, mr, k, lane + 32 * c));
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            g[k].set(c, sget<S, NV, C>(stage, 9 + k, ex4(k), lane + 32 * c));
+            g[k].set(c, spop<S, NV, C>(p, stage, mr, 9 + k, lane + 32 * c));
     }
 }
 
 // rho u_r of the streamed populations in strip column col of a stage
 template <class S, int NV, class C>
-__device__ __forceinline__ C stage_jr(const S *stage, int col)
+__device__ __forceinline__ C stage_jr(const StepParams<C> &p, const S *stage, const MRows &mr, int col)
 {
-    return (sget<S, NV, C>(stage, 2, 0, col) - sget<S, NV, C>(stage, 4, 0, col)) +
-           (sget<S, NV, C>(stage, 5, 1, col) - sget<S, NV, C>(stage, 8, 1, col)) +
-           (sget<S, NV, C>(stage, 6, -1, col) - sget<S, NV, C>(stage, 7, -1, col));
+    return (spop<S, NV, C>(p, stage, mr, 2, col) - spop<S, NV, C>(p, stage, mr, 4, col)) +
+           (spop<S, NV, C>(p, stage, mr, 5, col) - spop<S, NV, C>(p, stage, mr, 8, col)) +
+           (spop<S, NV, C>(p, stage, mr, 6, col) - spop<S, NV, C>(p, stage, mr, 7, col));
 }
 
 // ---- the fused step kernel ------------------------------------------------------------
 // collide row j of the tile from its stage and write it (and its ghosts)
 template <class S, int NV, class C>
 __device__ __forceinline__ void collide_row(const StepParams<C> &p, const S *src, S *__restrict__ dst, const S *st,
-                                            int x0, int lane, int j, int64_t t, const Mom<Vec<C, NV>> &mp,
-                                            const Mom<Vec<C, NV>> &mc, const Mom<Vec<C, NV>> &mn, const float2 *stab)
+                                            const MRows &mr, int x0, int lane, int j, int64_t t,
+                                            const Mom<Vec<C, NV>> &mp, const Mom<Vec<C, NV>> &mc,
+                                            const Mom<Vec<C, NV>> &mn, const float2 *stab)
 {
     using V = Vec<C, NV>;
     // axial neighbours of rho u_r: the strip's columns form one sequence
@@ -808,7 +1007,7 @@ __device__ __forceinline__ void collide_row(const StepParams<C> &p, const S *src
     V left, right;
     // rho u_r beside the strip, computed by every lane for its half's side
     // (lanes 0..15 the left, 16..31 the right) in one warp-uniform pass
-    const C beside = stage_jr<S, NV, C>(st, lane < 16 ? -1 : 32 * NV);
+    const C beside = stage_jr<S, NV, C>(p, st, mr, lane < 16 ? -1 : 32 * NV);
 #pragma unroll
     for (int c = 0; c < NV; ++c) {
         const C up = __shfl_up_sync(0xffffffffu, mc.jr[c], 1);
@@ -831,7 +1030,7 @@ __device__ __forceinline__ void collide_row(const StepParams<C> &p, const S *src
     if (x0 + lane >= p.nx)
         return;  // no active node in this lane
     V f[9], g[4], fo[9], go[4];
-    stage_pops<S, NV, C>(st, lane, f, g);
+    stage_pops<S, NV, C>(p, st, mr, lane, f, g);
     const C inv_r = C(1) / (p.r0 + C(j) + C(0.5));
     collide<C, V>(p, f, g, mc, inv_r, C(0.5) * (mn.jx - mp.jx), C(0.5) * (mn.jr - mp.jr), C(0.5) * (right - left),
                   C(0.5) * (mn.dT - mp.dT), fo, go, stab);
@@ -841,12 +1040,28 @@ __device__ __forceinline__ void collide_row(const StepParams<C> &p, const S *src
         const int i = x0 + lane + 32 * c;
         if (i < p.nx) {
             const unsigned o = (unsigned)((j + 1) * p.pitch + i + PAD_COLS);
+            if constexpr (IsSplit<S>::value) {
+                // the node's pre-collision moments, and every population as its deviation
+                // from the linear part at them
+                const C jx = mc.jx[c], jr = mc.jr[c], dT = mc.dT[c];
+                float *M = split_m(dst, p.plane);
+                M[o] = jx;
+                M[o + pl] = jr;
+                M[o + 2 * pl] = dT;
 #pragma unroll
-            for (int k = 0; k < 9; ++k)
-                dst[o + k * pl] = store_as<S, C>(fo[k][c]);
+                for (int k = 0; k < 9; ++k)
+                    dst[o + k * pl] = store_as<S, C>(fo[k][c] - lin_part<C>(p, k, jx, jr, dT));
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                dst[o + (9 + k) * pl] = store_as<S, C>(go[k][c]);
+                for (int k = 0; k < 4; ++k)
+                    dst[o + (9 + k) * pl] = store_as<S, C>(go[k][c] - lin_part<C>(p, 9 + k, jx, jr, dT));
+            } else {
+#pragma unroll
+                for (int k = 0; k < 9; ++k)
+                    dst[o + k * pl] = store_as<S, C>(fo[k][c]);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    dst[o + (9 + k) * pl] = store_as<S, C>(go[k][c]);
+            }
             if (i == 0 || i == p.nx - 1 || j == 0 || j == p.nr - 1)
                 write_ghosts<S, C>(p, dst, i, j, t + 1);
         }
@@ -854,69 +1069,121 @@ __device__ __forceinline__ void collide_row(const StepParams<C> &p, const S *src
 }
 
 // One warp tile: columns x0..x0+32 NV-1 of rows j0..j1-1.  Rows j0-1 (if
-// any) through min(j1, nr-1) are staged in order, NSTAGE - 2 rows ahead of
-// the one whose moments are being formed; row j is collided once the
-// moments of row j + 1 exist.  (The stage being refilled is never one of
-// the two being read: it held row idx - 2.)
+// any) through min(j1, nr-1) are staged one after the other, NSTAGE - 2
+// rows ahead of the one whose moments are being formed; a row is collided
+// once the moments of the rows on both sides of it exist.  (The stage being
+// refilled is never one of the two being read: it held row idx - 2.)
+//
+// FP32 storage: even bands march upwards and odd bands downwards.  The two
+// rows that neighbouring bands share (each one's last own row and the
+// other's halo row) are then staged by both tiles at the same end of their
+// work, a fraction of a microsecond apart (the tiles of one strip are one
+// band of work items apart), so the second read finds them in L2.  With
+// one direction the second read came a whole tile later, after some 90 MB
+// of other traffic, and about a fifth of them went to DRAM again.  The
+// 2-byte kernels, bound by instruction issue, keep one direction.
+//
+// Moment-split storage also stages moment rows rfirst - 1 .. min(j1, nr -
+// 1) + 1 into the warp's ring msm, one row further ahead (row r + 1 lands
+// with the populations of row r); the slot refilled held row r - 3.
 template <class S, int NV, class C>
 __device__ __forceinline__ void step_tile(const StepParams<C> &p, const S *__restrict__ src, S *__restrict__ dst,
-                                          S *wsm, int tile, int lane, int64_t t, const float2 *stab = nullptr)
+                                          S *wsm, int tile, int lane, int64_t t, const float2 *stab = nullptr,
+                                          float *msm = nullptr)
 {
     using Wn = Win<S, NV>;
     using V = Vec<C, NV>;
     constexpr int NSTAGE = Stages<NV>::value;
     constexpr int D = NSTAGE - 2;
+    constexpr bool SPLIT = IsSplit<S>::value;
+    constexpr bool ALT = std::is_same<S, float>::value;  // alternating band directions
+    static_assert(!SPLIT || D == 1, "the moment ring assumes populations staged one row ahead");
     const int strip = tile % p.nstrips;
     const int band = tile / p.nstrips;
     const int x0 = strip * 32 * NV;
     const int j0 = band * p.band;
     const int j1 = min(j0 + p.band, p.nr);
-    const int rfirst = j0 > 0 ? j0 - 1 : j0;
-    const int nrows = min(j1, p.nr - 1) - rfirst + 1;
+    const int rlo = j0 > 0 ? j0 - 1 : j0;  // rows staged: rlo .. rhi
+    const int rhi = min(j1, p.nr - 1);
+    const int nrows = rhi - rlo + 1;
+    const bool down = ALT && (band & 1) != 0;
+    const int rstart = down ? rhi : rlo;
+    const int dr = down ? -1 : 1;
+    const int first_own = down ? j1 - 1 : j0;            // first row of the band reached
+    const bool edge_first = down ? j1 == p.nr : j0 == 0;  // the lattice ends beyond it
+    const bool edge_last = down ? j0 == 0 : j1 == p.nr;   // ... beyond the last one
     const CopyPlan<S, NV> plan = make_copy_plan<S, NV, C>(p, x0, lane);
+    const float *M = nullptr;
+    if constexpr (SPLIT)
+        M = split_m(src, p.plane);
+    // moment row m lives in slot (m - rlo + 1) % MSLOTS
+    auto mslot = [&](int m) { return msm + ((m - rlo + 1) % MSLOTS) * MWin<NV>::SLOT; };
+    auto mrows = [&](int r) {
+        MRows mr = {{nullptr, nullptr, nullptr}};
+        if constexpr (SPLIT)
+            mr = MRows{{mslot(r - 1), mslot(r), mslot(r + 1)}};
+        return mr;
+    };
 
+    if constexpr (SPLIT) {  // moment rows rlo - 1 .. rlo + 1 join the first group
+        for (int m = rlo - 1; m <= rlo + 1; ++m)
+            issue_mrow<NV, C>(p, M, mslot(m), x0, m, lane);
+    }
 #pragma unroll
     for (int t = 0; t < D; ++t) {
         if (t < nrows)
-            issue_row<S, NV, C>(p, src, wsm + t * Wn::STAGE, plan, rfirst + t, lane);
+            issue_row<S, NV, C>(p, src, wsm + t * Wn::STAGE, plan, rstart + dr * t, lane);
         cp_async_commit();
     }
-    Mom<V> mp, mc;
+    Mom<V> mb, mc;  // moments of the row passed before the current one, and of the current one
 #pragma unroll 1
     for (int idx = 0; idx < nrows; ++idx) {
         __syncwarp();  // every lane is done with the stage refilled next
         if (idx + D < nrows)
-            issue_row<S, NV, C>(p, src, wsm + ((idx + D) % NSTAGE) * Wn::STAGE, plan, rfirst + idx + D, lane);
+            issue_row<S, NV, C>(p, src, wsm + ((idx + D) % NSTAGE) * Wn::STAGE, plan, rstart + dr * (idx + D), lane);
+        if constexpr (SPLIT) {
+            if (idx + D < nrows)  // moment rows up to the last staged row + 1 (at most the ghost row nr)
+                issue_mrow<NV, C>(p, M, mslot(rlo + idx + D + 1), x0, rlo + idx + D + 1, lane);
+        }
         cp_async_commit();
         cp_async_wait<D>();
         __syncwarp();  // row idx has landed for every lane
-        const int r = rfirst + idx;
+        const int r = rstart + dr * idx;
         const S *st = wsm + (idx % NSTAGE) * Wn::STAGE;
         V f[9], g[4];
-        stage_pops<S, NV, C>(st, lane, f, g);
+        stage_pops<S, NV, C>(p, st, mrows(r), lane, f, g);
         const Mom<V> mr = moments<V>(f, g);
-        if (r < j0) {
-            mp = mr;
-        } else if (r == j0) {
-            if (j0 == 0)
-                mp = ghost_bottom<C, V>(p, mr);
+        if (r == first_own) {
+            if (edge_first)
+                mb = down ? ghost_top<C, V>(p, mr) : ghost_bottom<C, V>(p, mr);
             mc = mr;
+        } else if (idx == 0) {  // the halo row
+            mb = mr;
         } else {
-            collide_row<S, NV, C>(p, src, dst, wsm + ((idx - 1) % NSTAGE) * Wn::STAGE, x0, lane, r - 1, t, mp, mc, mr,
-                                  stab);
-            mp = mc;
+            collide_row<S, NV, C>(p, src, dst, wsm + ((idx - 1) % NSTAGE) * Wn::STAGE, mrows(r - dr), x0, lane,
+                                  r - dr, t, down ? mr : mb, mc, down ? mb : mr, stab);
+            mb = mc;
             mc = mr;
         }
     }
-    if (j1 == p.nr)
-        collide_row<S, NV, C>(p, src, dst, wsm + ((nrows - 1) % NSTAGE) * Wn::STAGE, x0, lane, p.nr - 1, t, mp, mc,
-                              ghost_top<C, V>(p, mc), stab);
+    if (edge_last)
+        collide_row<S, NV, C>(p, src, dst, wsm + ((nrows - 1) % NSTAGE) * Wn::STAGE, mrows(down ? 0 : p.nr - 1), x0,
+                              lane, down ? 0 : p.nr - 1, t, down ? ghost_bottom<C, V>(p, mc) : mb, mc,
+                              down ? mb : ghost_top<C, V>(p, mc), stab);
     cp_async_wait<0>();
     __syncwarp();
 }
 
 template <class S, class C>
 constexpr int step_smem_per_warp()
+{
+    constexpr int NV = NodesPerLane<C>::value;
+    return Stages<NV>::value * Win<S, NV>::STAGE * (int)sizeof(S) +
+           (IsSplit<S>::value ? MSLOTS * MWin<NV>::SLOT * (int)sizeof(float) : 0);
+}
+
+template <class S, class C>
+constexpr int pop_ring_bytes()
 {
     constexpr int NV = NodesPerLane<C>::value;
     return Stages<NV>::value * Win<S, NV>::STAGE * (int)sizeof(S);
@@ -1047,7 +1314,9 @@ __global__ void __launch_bounds__(256) step_run_kernel(const __grid_constant__ S
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    S *wsm = reinterpret_cast<S *>(smem_raw) + (size_t)warp * Stages<NV>::value * Win<S, NV>::STAGE;
+    unsigned char *wbase = smem_raw + (size_t)warp * step_smem_per_warp<S, C>();
+    S *wsm = reinterpret_cast<S *>(wbase);
+    float *msm = IsSplit<S>::value ? reinterpret_cast<float *>(wbase + pop_ring_bytes<S, C>()) : nullptr;
     const float2 *stab = nullptr;
     if constexpr (UseSmemTable<S, C>::value) {
         if (p.ntab > 1 && p.ntab <= SMEM_TAB) {
@@ -1082,7 +1351,7 @@ __global__ void __launch_bounds__(256) step_run_kernel(const __grid_constant__ S
         S *dst = static_cast<S *>((k & 1) ? const_cast<void *>(p.src) : p.dst);
         const int s1 = min((g + 1) * ctl.group, p.nstrips);
         for (int s = g * ctl.group; s < s1; ++s)
-            step_tile<S, NV, C>(p, src, dst, wsm, b * p.nstrips + s, lane, p.step + k, stab);
+            step_tile<S, NV, C>(p, src, dst, wsm, b * p.nstrips + s, lane, p.step + k, stab, msm);
         red_release_add(ctl.flags + item, 1u);
         n = __shfl_sync(0xffffffffu, next, 0);
     }
@@ -1116,7 +1385,9 @@ __global__ void __launch_bounds__(256) batch_run_kernel(const TileRef *__restric
     const int wpc = blockDim.x >> 5;
     // parameter blocks of all warps first, then the warps' staging rings
     StepParams<C> *pw = reinterpret_cast<StepParams<C> *>(smem_raw) + warp;
-    S *wsm = reinterpret_cast<S *>(smem_raw + wpc * sizeof(StepParams<C>)) + (size_t)warp * Stages<NV>::value * Win<S, NV>::STAGE;
+    unsigned char *wbase = smem_raw + wpc * sizeof(StepParams<C>) + (size_t)warp * step_smem_per_warp<S, C>();
+    S *wsm = reinterpret_cast<S *>(wbase);
+    float *msm = IsSplit<S>::value ? reinterpret_cast<float *>(wbase + pop_ring_bytes<S, C>()) : nullptr;
     static_assert(sizeof(StepParams<C>) % 16 == 0 && PW <= 32, "parameter block copy");
     const unsigned total = (unsigned)ctl.nsteps * (unsigned)ntiles;
     unsigned n = 0;
@@ -1144,7 +1415,7 @@ __global__ void __launch_bounds__(256) batch_run_kernel(const TileRef *__restric
         }
         const S *src = static_cast<const S *>((k & 1) ? p.dst : p.src);
         S *dst = static_cast<S *>((k & 1) ? const_cast<void *>(p.src) : p.dst);
-        step_tile<S, NV, C>(p, src, dst, wsm, t.tile, lane, p.step + k);
+        step_tile<S, NV, C>(p, src, dst, wsm, t.tile, lane, p.step + k, nullptr, msm);
         red_release_add(ctl.flags + idx, 1u);
         n = __shfl_sync(0xffffffffu, next, 0);
     }
@@ -1338,6 +1609,69 @@ __global__ void state_out_kernel(const S *buf, double *f, double *g, int nx, int
         f[(int64_t)q * N + c] = v + w9<double>(q) * rho0;
     else
         g[(int64_t)(q - 9) * N + c] = v + 0.25 * T0;
+}
+
+// ---- moment-split storage: state conversion, one node per thread ----------------------
+// A minimal parameter block for lin_part: T0 and 1 / (2 rho0), formed exactly as the host
+// forms them for the step kernels.
+__device__ __forceinline__ StepParams<float> lin_params(double rho0, double T0)
+{
+    StepParams<float> p;
+    p.T0 = float(T0);
+    p.hir0 = float(0.5 / rho0);
+    return p;
+}
+
+template <class S>
+__global__ void split_state_in_kernel(S *buf, const double *f, const double *g, int nx, int nr, int pitch,
+                                      int64_t plane, double rho0, double T0)
+{
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t N = (int64_t)nx * nr;
+    if (n >= N)
+        return;
+    const int i = (int)(n % nx), j = (int)(n / nx);
+    const StepParams<float> lp = lin_params(rho0, T0);
+    double dev[13], jx = 0.0, jr = 0.0, dT = 0.0;
+    for (int k = 0; k < 9; ++k) {
+        dev[k] = f[(int64_t)k * N + n] - w9<double>(k) * rho0;
+        jx += ex9(k) * dev[k];
+        jr += ey9(k) * dev[k];
+    }
+    for (int k = 0; k < 4; ++k) {
+        dev[9 + k] = g[(int64_t)k * N + n] - 0.25 * T0;
+        dT += dev[9 + k];
+    }
+    const float mx = float(jx), mr = float(jr), mT = float(dT);
+    const int64_t o = (int64_t)(j + 1) * pitch + (i + PAD_COLS);
+    float *M = split_m(buf, plane);
+    M[o] = mx;
+    M[plane + o] = mr;
+    M[2 * plane + o] = mT;
+    for (int q = 0; q < 13; ++q)
+        buf[(int64_t)q * plane + o] = store_as<S, float>(float(dev[q]) - lin_part<float>(lp, q, mx, mr, mT));
+}
+
+template <class S>
+__global__ void split_state_out_kernel(const S *buf, double *f, double *g, int nx, int nr, int pitch, int64_t plane,
+                                       double rho0, double T0)
+{
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t N = (int64_t)nx * nr;
+    if (n >= N)
+        return;
+    const int i = (int)(n % nx), j = (int)(n / nx);
+    const StepParams<float> lp = lin_params(rho0, T0);
+    const int64_t o = (int64_t)(j + 1) * pitch + (i + PAD_COLS);
+    const float *M = split_m(buf, plane);
+    const float mx = M[o], mr = M[plane + o], mT = M[2 * plane + o];
+    for (int q = 0; q < 13; ++q) {
+        const double v = double(lin_part<float>(lp, q, mx, mr, mT) + load_as<S, float>(buf + (int64_t)q * plane + o));
+        if (q < 9)
+            f[(int64_t)q * N + n] = v + w9<double>(q) * rho0;
+        else
+            g[(int64_t)(q - 9) * N + n] = v + 0.25 * T0;
+    }
 }
 
 }  // namespace lbm

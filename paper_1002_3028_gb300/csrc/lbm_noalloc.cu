@@ -104,6 +104,8 @@ extern "C" int lbm_diagnostics_noalloc(lbm_lattice *h, lbm_diag *out, lbm_stream
     case LBM_F64: e = launch_rows<double, double>(v.pd, v.prev_valid, scratch, s); break;
     case LBM_F32: e = launch_rows<float, float>(v.pf, v.prev_valid, scratch, s); break;
     case LBM_F16: e = launch_rows<__half, float>(v.pf, v.prev_valid, scratch, s); break;
+    case LBM_F16S: e = launch_rows<half_s, float>(v.pf, v.prev_valid, scratch, s); break;
+    case LBM_BF16S: e = launch_rows<bf16_s, float>(v.pf, v.prev_valid, scratch, s); break;
     default: e = launch_rows<__nv_bfloat16, float>(v.pf, v.prev_valid, scratch, s); break;
     }
     double vals[DIAG_SLOTS];

@@ -111,23 +111,36 @@ cudaError_t LBM_CAT(launch_diag_, LBM_TAG)(const StepParams<LBM_C> &p, int have_
 cudaError_t LBM_CAT(launch_state_in_, LBM_TAG)(void *buf, const double *f, const double *g, int nx, int nr, int pitch,
                                                int64_t plane, double rho0, double T0, cudaStream_t s)
 {
-    const int64_t n = 13 * (int64_t)nx * nr;
     const int threads = 256;
+#ifdef LBM_SPLIT  // one node per thread: the node's moments first
+    const int64_t n = (int64_t)nx * nr;
+    split_state_in_kernel<LBM_S><<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(
+        static_cast<LBM_S *>(buf), f, g, nx, nr, pitch, plane, rho0, T0);
+#else
+    const int64_t n = 13 * (int64_t)nx * nr;
     state_in_kernel<LBM_S><<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(
         static_cast<LBM_S *>(buf), f, g, nx, nr, pitch, plane, rho0, T0);
+#endif
     return cudaGetLastError();
 }
 
 cudaError_t LBM_CAT(launch_state_out_, LBM_TAG)(const void *buf, double *f, double *g, int nx, int nr, int pitch,
                                                 int64_t plane, double rho0, double T0, cudaStream_t s)
 {
-    const int64_t n = 13 * (int64_t)nx * nr;
     const int threads = 256;
+#ifdef LBM_SPLIT
+    const int64_t n = (int64_t)nx * nr;
+    split_state_out_kernel<LBM_S><<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(
+        static_cast<const LBM_S *>(buf), f, g, nx, nr, pitch, plane, rho0, T0);
+#else
+    const int64_t n = 13 * (int64_t)nx * nr;
     state_out_kernel<LBM_S><<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(
         static_cast<const LBM_S *>(buf), f, g, nx, nr, pitch, plane, rho0, T0);
+#endif
     return cudaGetLastError();
 }
 
+#ifndef LBM_SPLIT  // moment-split storage has no AA layout
 // ---- AA layout ------------------------------------------------------------------------
 cudaError_t LBM_CAT(launch_aa_run_, LBM_TAG)(const StepParams<LBM_C> &p, const RunCtl &ctl, int warps_per_cta, int ctas,
                                              cudaStream_t s)
@@ -203,5 +216,7 @@ cudaError_t LBM_CAT(launch_aa_state_out_, LBM_TAG)(const void *buf, int phase, d
         static_cast<const LBM_S *>(buf), phase, f, g, nx, nr, pitch, plane, rho0, T0);
     return cudaGetLastError();
 }
+
+#endif  // LBM_SPLIT
 
 }  // namespace lbm

@@ -20,7 +20,9 @@ from .inputs import LatticeConfig, Workload
 
 LBM_OK = 0
 ERRORS = {-1: "LBM_ERR_INVALID_ARG", -2: "LBM_ERR_OOM", -3: "LBM_ERR_CUDA", -4: "LBM_ERR_DIVERGED"}
-STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "f16s": 4, "bf16s": 5}
+# moment-split storage: FP32 moments beside 2-byte deviations from the linear equilibrium
+SPLIT = ("f16s", "bf16s")
 _BC_IN = {"inlet": 0, "periodic": 1}
 _BC_OUT = {"outflow": 0, "wall": 1, "periodic": 2}
 _BC_TOP = {"wall": 0, "open": 1}
@@ -313,14 +315,23 @@ class Lattice:
         # keep the inputs alive until the conversion kernel has run
         torch.cuda.current_stream(self.device).synchronize() if stream is None else stream.synchronize()
 
+    def _checkpoint_shape(self):
+        import torch
+
+        if self.storage in SPLIT:  # 13 planes of 2-byte deviations, then 3 FP32 moment planes, as bytes
+            return (13 * 2 + 3 * 4) * self.nr * self.nx, torch.uint8
+        dt = {"f64": torch.float64, "f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[self.storage]
+        return (13, self.nr, self.nx), dt
+
     def save(self, stream=None):
-        """Checkpoint: (stored deviations (13, nr, nx) in the storage type, step count); exact."""
+        """Checkpoint: (stored state in the storage type, step count); exact.  The state is the
+        deviations (13, nr, nx); for moment-split storage the raw bytes of lbm_save's layout."""
         import torch
 
         n = C.c_size_t()
         _check(self._L.lbm_checkpoint_bytes(self._h, C.byref(n)), "lbm_checkpoint_bytes")
-        dt = {"f64": torch.float64, "f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[self.storage]
-        out = torch.empty((13, self.nr, self.nx), dtype=dt, device=self.device)
+        shape, dt = self._checkpoint_shape()
+        out = torch.empty(shape, dtype=dt, device=self.device)
         assert out.numel() * out.element_size() == n.value
         _check(self._L.lbm_save(self._h, C.c_void_p(out.data_ptr()), _stream_ptr(stream)), "lbm_save")
         return out, self.step_count
@@ -331,13 +342,26 @@ class Lattice:
 
         n = C.c_size_t()
         _check(self._L.lbm_checkpoint_bytes(self._h, C.byref(n)), "lbm_checkpoint_bytes")
-        if tuple(planes.shape) != (13, self.nr, self.nx) or planes.numel() * planes.element_size() != n.value:
+        shape, _ = self._checkpoint_shape()
+        if tuple(planes.shape) != tuple(shape if isinstance(shape, tuple) else (shape,)) or \
+                planes.numel() * planes.element_size() != n.value:
             raise ValueError("checkpoint does not match this lattice")
         planes = planes.to(self.device).contiguous()
         _check(self._L.lbm_restore(self._h, C.c_void_p(planes.data_ptr()), int(step), _stream_ptr(stream)),
                "lbm_restore")
         # keep the input alive until the copies have run
         torch.cuda.current_stream(self.device).synchronize() if stream is None else stream.synchronize()
+
+    def restore_async(self, planes, step: int, stream=None):
+        """``restore`` from a device tensor without synchronising: the caller keeps ``planes``
+        alive until the stream has run the copies."""
+        n = C.c_size_t()
+        _check(self._L.lbm_checkpoint_bytes(self._h, C.byref(n)), "lbm_checkpoint_bytes")
+        if (planes.numel() * planes.element_size() != n.value
+                or planes.device != self.device or not planes.is_contiguous()):
+            raise ValueError("checkpoint does not match this lattice (a contiguous device tensor)")
+        _check(self._L.lbm_restore(self._h, C.c_void_p(planes.data_ptr()), int(step), _stream_ptr(stream)),
+               "lbm_restore")
 
 
 class Batch:

@@ -54,6 +54,17 @@ def test_required_bytes_counts_two_buffers():
         n = lbm.required_bytes(cfg, st)
         two = 2 * 13 * pitch * (40 + 2) * sz
         assert two <= n < two + 200_000
+    for st in ("f16s", "bf16s"):  # 13 two-byte planes and 3 FP32 moment planes per buffer
+        n = lbm.required_bytes(cfg, st)
+        two = 2 * (13 * 2 + 3 * 4) * pitch * (40 + 2)
+        assert two <= n < two + 200_000
+
+
+def test_moment_split_storage_has_no_aa_pattern():
+    d = lbm.make_desc(I.LatticeConfig(nx=40, nr=10), "f16s", pattern="aa")
+    n = C.c_size_t(0)
+    assert lbm.lib().lbm_required_bytes(C.byref(d), C.byref(n)) == -1
+    assert "two-buffer" in lbm.lib().lbm_last_error().decode()
 
 
 @pytest.mark.parametrize("bad", [

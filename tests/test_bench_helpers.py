@@ -23,13 +23,13 @@ def test_kernel_hash_ignores_comments(tmp_path, monkeypatch):
     assert bench.kernel_hash() != ha
 
 
-@pytest.mark.parametrize("pattern", ["ab", "aa"])
-@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("storage,pattern", [("f32", "ab"), ("f16", "ab"), ("f16s", "ab"), ("bf16s", "ab"),
+                                             ("f32", "aa"), ("f16", "aa")])
 def test_committed_ncu_summaries_belong_to_the_current_kernel(storage, pattern):
     """The traffic figure bench.py reports comes from a capture of the kernel code as it is
     (the AA pattern's FP16 buffer partly stays in L2, hence the lower bound)."""
     t = bench.ncu_traffic(storage, "jet4096x1024", pattern)
-    assert t is not None and 0.9 * 52 * (2 if storage == "f32" else 1) * 4096 * 1024 < t
+    assert t is not None and 0.9 * bench.bytes_per_lup(storage) * 4096 * 1024 < t
 
 
 def test_kernel_hash_of_the_aa_pattern_covers_its_own_source():

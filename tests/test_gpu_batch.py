@@ -44,7 +44,7 @@ def states_equal(a, b):
     return torch.equal(fa, fb) and torch.equal(ga, gb)
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16", "f16s", "bf16s"])
 def test_batch_members_match_standalone(lbm, storage):
     ws = ragged_jets(5, 3)
     alone = [lbm.Lattice.from_workload(w, storage) for w in ws]
@@ -136,7 +136,7 @@ def test_batch_member_matches_oracle(lbm, orc):
         assert np.max(np.abs(gg[q].cpu().numpy() - go[q])) <= 1e-12 * np.max(np.abs(go[q]))
 
 
-@pytest.mark.parametrize("storage,bar", [("f32", 2e-5), ("f16", 2e-3)])
+@pytest.mark.parametrize("storage,bar", [("f32", 2e-5), ("f16", 2e-3), ("f16s", 2e-3)])
 def test_full_ensemble_batch_matches_oracle(lbm, orc, storage, bar):
     """The benchmark's ensemble (256 ragged jets, 23.2 M nodes) in its own launch
     configuration: two batched steps from random states on sampled members, against the

@@ -17,7 +17,7 @@ def lbm():
     return L
 
 
-@pytest.mark.parametrize("storage", ["f16", "f32"])
+@pytest.mark.parametrize("storage", ["f16", "f32", "f16s"])
 def test_results_alone_equal_results_in_the_mix(lbm, storage):
     from paper_1002_3028_gb300.serve import GpuBatchEngine, serve
 
