@@ -77,8 +77,8 @@ typedef enum {
  *       2-byte rounding then scales with the non-equilibrium and quadratic
  *       parts, not with the velocity or the temperature excess: 76 bytes per
  *       lattice update instead of 52.  Two-buffer pattern only.  A checkpoint
- *       (lbm_save) holds the 13 population planes, then the three moment
- *       planes (j_x, j_r, T - T0) in FP32. */
+ *       (lbm_save) holds the 13 population planes, then the (j_x, j_r)
+ *       pairs of every node (FP32, interleaved), then T - T0 (FP32). */
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3, LBM_F16S = 4, LBM_BF16S = 5 } lbm_storage;
 
 typedef enum { LBM_IN_INLET = 0, LBM_IN_PERIODIC = 1 } lbm_bc_in;

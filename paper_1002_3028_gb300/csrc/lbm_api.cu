@@ -1334,13 +1334,15 @@ static int copy_planes(lbm_lattice *h, void *dense, bool out, cudaStream_t s)
         if (e != cudaSuccess)
             return cuda_fail(e, "checkpoint plane copy");
     }
-    if (is_split(h->d.storage)) {  // the moment planes follow the 13 population planes
-        const size_t mrow = (size_t)h->d.nx * 4, mpitch = (size_t)h->L.pitch * 4;
+    if (is_split(h->d.storage)) {  // then the (j_x, j_r) pairs, then T - T0, without ghosts or padding
         char *mbase = buf + lbm::split_moff(h->L.plane);
         char *mflat = static_cast<char *>(dense) + (size_t)13 * (size_t)h->d.nr * row;
-        for (int m = 0; m < lbm::SPLIT_MOMENTS; ++m) {
-            char *padded = mbase + ((size_t)m * (size_t)h->L.plane + (size_t)h->L.pitch + lbm::PAD_COLS) * 4;
-            char *flat = mflat + (size_t)m * (size_t)h->d.nr * mrow;
+        for (int m = 0; m < 2; ++m) {  // m = 0: pairs (8 bytes a node), m = 1: T - T0 (4 bytes)
+            const size_t es_m = m == 0 ? 8 : 4;
+            const size_t mrow = (size_t)h->d.nx * es_m, mpitch = (size_t)h->L.pitch * es_m;
+            char *padded = mbase + (m == 0 ? 0 : (size_t)h->L.plane * 8) +
+                           ((size_t)h->L.pitch + lbm::PAD_COLS) * es_m;
+            char *flat = mflat + (m == 0 ? 0 : (size_t)h->d.nr * (size_t)h->d.nx * 8);
             cudaError_t e = out ? cudaMemcpy2DAsync(flat, mrow, padded, mpitch, mrow, h->d.nr, cudaMemcpyDeviceToDevice, s)
                                 : cudaMemcpy2DAsync(padded, mpitch, flat, mrow, mrow, h->d.nr, cudaMemcpyDeviceToDevice, s);
             if (e != cudaSuccess)

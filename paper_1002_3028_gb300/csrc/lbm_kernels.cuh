@@ -129,8 +129,9 @@ template <> __device__ __forceinline__ __nv_bfloat16 store_as<__nv_bfloat16, flo
 
 // ---- moment-split storage of 2-byte types ------------------------------------
 // Storage types half_s and bf16_s keep, for every cell, the moments
-// j_x = rho u_x, j_r = rho u_r and T - T0 in three FP32 planes (after the 13
-// population planes of the buffer, at byte offset split_moff(plane)), and
+// j_x = rho u_x, j_r = rho u_r and T - T0 in FP32 (after the 13 population
+// planes of the buffer, at byte offset split_moff(plane): a plane of
+// (j_x, j_r) pairs, 2 plane floats, then a plane of T - T0), and
 // each population as its 2-byte deviation d from the part of the equilibrium
 // that is linear in those moments:
 //   f_k - w_k rho0 = 3 w_k e_k.j + d_k,
@@ -162,6 +163,14 @@ template <> __device__ __forceinline__ float load_as_shared<half_s, float>(const
 template <> __device__ __forceinline__ float load_as_shared<bf16_s, float>(const bf16_s *p) { return __bfloat162float(p->v); }
 template <> __device__ __forceinline__ half_s store_as<half_s, float>(float v) { return half_s{__float2half_rn(v)}; }
 template <> __device__ __forceinline__ bf16_s store_as<bf16_s, float>(float v) { return bf16_s{__float2bfloat16_rn(v)}; }
+
+// the moments of cell offset o (an element offset within a plane) in a moment area M
+struct MomRef {
+    float *M;
+    int64_t plane;
+    __device__ __forceinline__ float2 &j(int64_t o) const { return reinterpret_cast<float2 *>(M)[o]; }
+    __device__ __forceinline__ float &T(int64_t o) const { return M[2 * plane + o]; }
+};
 
 template <class S>
 __device__ __forceinline__ float *split_m(S *buf, int64_t plane)
@@ -474,9 +483,10 @@ __device__ __noinline__ void write_ghosts(const StepParams<C> &p, S *buf, int i,
     if constexpr (IsSplit<S>::value) {
         // the node's stored populations (its moments plus the stored deviations), then each
         // ghost value as a deviation from the linear part at the ghost cell's own moments
-        float *M = split_m(buf, p.plane);
+        const MomRef M{split_m(buf, p.plane), p.plane};
         const int64_t o = cell(p, 0, i, j);
-        const C jx = M[o], jr = M[p.plane + o], dT = M[2 * p.plane + o];  // plain loads: this thread stored them
+        const float2 jj = M.j(o);  // plain loads: this thread stored them
+        const C jx = jj.x, jr = jj.y, dT = M.T(o);
 #pragma unroll
         for (int k = 0; k < 9; ++k)
             fo[k] = lin_part<C>(p, k, jx, jr, dT) + load_as_shared<S, C>(buf + cell(p, k, i, j));
@@ -487,9 +497,8 @@ __device__ __noinline__ void write_ghosts(const StepParams<C> &p, S *buf, int i,
             C gx, gr, gT;
             const int64_t oc = cell(p, 0, ci, cj);
             if (ghost_moments<C>(p, ci, cj, jx, jr, dT, gx, gr, gT)) {
-                M[oc] = gx;
-                M[p.plane + oc] = gr;
-                M[2 * p.plane + oc] = gT;
+                M.j(oc) = make_float2(gx, gr);
+                M.T(oc) = gT;
                 v -= lin_part<C>(p, q, gx, gr, gT);
             }
             buf[cell(p, q, ci, cj)] = store_as<S, C>(v);
@@ -524,8 +533,10 @@ __device__ __forceinline__ C pulled(const StepParams<C> &p, const S *src, int q,
     const int64_t c = stream_cell(p, q, i, j);
     C v = load_as<S, C>(src + c);
     if constexpr (IsSplit<S>::value) {  // plus the linear part at the source cell's moments
-        const float *M = split_m(src, p.plane) + (c - (int64_t)q * p.plane);
-        v += lin_part<C>(p, q, __ldcg(M), __ldcg(M + p.plane), __ldcg(M + 2 * p.plane));
+        const float *M = split_m(src, p.plane);
+        const int64_t o = c - (int64_t)q * p.plane;
+        const float2 jj = __ldcg(reinterpret_cast<const float2 *>(M) + o);
+        v += lin_part<C>(p, q, jj.x, jj.y, __ldcg(M + 2 * p.plane + o));
     }
     return v;
 }
@@ -914,28 +925,40 @@ __device__ __forceinline__ C sget(const S *stage, int q, int ex, int col)
 }
 
 // Moment-split storage: the moment rows are staged too, each lattice row
-// once, into a per-warp ring of MSLOTS slots; a slot holds the three FP32
-// moment planes of one row over the strip's columns and MH columns on each
-// side.  A row's populations come from sources in rows r - 1, r and r + 1,
-// so the pull of row r reads three slots.
+// once, into a per-warp ring of MSLOTS slots; a slot holds one row's
+// (j_x, j_r) pairs and its T - T0 over the strip's columns and MH columns
+// on each side.  A row's populations come from sources in rows r - 1, r and
+// r + 1, so the pull of row r reads three slots: the (j_x, j_r) pairs of
+// the eight neighbours and T - T0 of the four axis neighbours, twelve
+// shared-memory loads per node.
 template <int NV> struct MWin {
-    static constexpr int H = 4;                    // halo columns (one 16-byte chunk) on each side
-    static constexpr int W = 32 * NV + 2 * H;      // window length per moment plane
-    static constexpr int CH = W / 4;               // 16-byte chunks per moment plane
-    static constexpr int SLOT = SPLIT_MOMENTS * W;  // floats per slot
+    static constexpr int H = 4;                // halo columns on each side
+    static constexpr int W = 32 * NV + 2 * H;  // window length (columns)
+    static constexpr int JCH = W / 2;          // 16-byte chunks of the (j_x, j_r) window
+    static constexpr int TCH = W / 4;          // 16-byte chunks of the T window
+    static constexpr int SLOT = 3 * W;         // floats per slot: W pairs, then W values of T
 };
 constexpr int MSLOTS = 5;  // moment rows r - 2 .. r + 2 around the row whose moments are formed
 
-// the staged moment windows of rows r - 1, r and r + 1 (null for other storage types)
+// this lane's view of the staged moment windows of rows r - 1, r, r + 1
+// (null for other storage types): element col of a window is strip column
+// lane + col
+template <int NV>
 struct MRows {
-    const float *row[3];
+    const float2 *j[3];
+    const float *T[3];
 };
 
-// moment m (0: j_x, 1: j_r, 2: T - T0) of strip column col in row r - ey
 template <int NV>
-__device__ __forceinline__ float mget(const MRows &mr, int ey, int m, int col)
+__device__ __forceinline__ MRows<NV> mrows_at(const float *const (&slot)[3], int lane)
 {
-    return mr.row[1 - ey][m * MWin<NV>::W + col + MWin<NV>::H];
+    MRows<NV> m;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        m.j[k] = reinterpret_cast<const float2 *>(slot[k]) + lane + MWin<NV>::H;
+        m.T[k] = slot[k] + 2 * MWin<NV>::W + lane + MWin<NV>::H;
+    }
+    return m;
 }
 
 // start the copies of moment row r into a slot
@@ -943,60 +966,102 @@ template <int NV, class C>
 __device__ __forceinline__ void issue_mrow(const StepParams<C> &p, const float *M, float *slot, int x0, int r, int lane)
 {
     using MW = MWin<NV>;
-    const int row = (r + 1) * p.pitch + x0 - MW::H + PAD_COLS;
+    const int c0 = (r + 1) * p.pitch + x0 - MW::H + PAD_COLS;  // element offset of the window's first cell
 #pragma unroll
-    for (int t0 = 0; t0 < SPLIT_MOMENTS * MW::CH; t0 += 32) {
+    for (int t0 = 0; t0 < MW::JCH + MW::TCH; t0 += 32) {
         const int t = t0 + lane;
-        if (t < SPLIT_MOMENTS * MW::CH) {
-            const int m = t / MW::CH, c = t - m * MW::CH;
-            cp_async16(slot + m * MW::W + 4 * c, M + (unsigned)(m * (int)p.plane + row + 4 * c));
-        }
+        if (t < MW::JCH)
+            cp_async16(slot + 4 * t, M + (unsigned)(2 * c0 + 4 * t));
+        else if (t < MW::JCH + MW::TCH)
+            cp_async16(slot + 2 * MW::W + 4 * (t - MW::JCH), M + (unsigned)(2 * (int)p.plane + c0 + 4 * (t - MW::JCH)));
     }
 }
 
-// population q of strip column col, pulled from the stage (plus its linear part for
-// moment-split storage)
+// population q of strip column lane + off pulled from the stage, with (moment-split
+// storage) its linear part at the source's moments
 template <class S, int NV, class C>
-__device__ __forceinline__ C spop(const StepParams<C> &p, const S *stage, const MRows &mr, int q, int col)
+__device__ __forceinline__ C spop(const StepParams<C> &p, const S *stage, const MRows<NV> &mr, int q, int lane, int off)
 {
     const int ex = qex(q), ey = qey(q);
-    C v = sget<S, NV, C>(stage, q, ex, col);
+    C v = sget<S, NV, C>(stage, q, ex, lane + off);
     if constexpr (IsSplit<S>::value) {
-        const int sc = col - ex;
-        v += lin_part<C>(p, q, mget<NV>(mr, ey, 0, sc), mget<NV>(mr, ey, 1, sc), q < 9 ? C(0) : mget<NV>(mr, ey, 2, sc));
+        const float2 jj = mr.j[1 - ey][off - ex];
+        v += lin_part<C>(p, q, jj.x, jj.y, q < 9 ? C(0) : mr.T[1 - ey][off - ex]);
     }
     return v;
 }
 
 template <class S, int NV, class C>
-__device__ __forceinline__ void stage_pops(const StepParams<C> &p, const S *stage, const MRows &mr, int lane,
+__device__ __forceinline__ void stage_pops(const StepParams<C> &p, const S *stage, const MRows<NV> &mr, int lane,
                                            Vec<C, NV> (&f)[9], Vec<C, NV> (&g)[4])
 {
+    using V = Vec<C, NV>;
 #pragma unroll
     for (int c = 0; c < NV; ++c) {
 #pragma unroll
         for (int k = 0; k < 9; ++k)
-            f[k].set(c, spop<S, NV, C>(p, stage, mr, k, lane + 32 * c));
+            f[k].set(c, sget<S, NV, C>(stage, k, ex9(k), lane + 32 * c));
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            g[k].set(c, spop<S, NV, C>(p, stage, mr, 9 + k, lane + 32 * c));
+            g[k].set(c, sget<S, NV, C>(stage, 9 + k, ex4(k), lane + 32 * c));
+    }
+    if constexpr (IsSplit<S>::value) {
+        // the linear parts, from the (j_x, j_r) pairs of the eight neighbours and T - T0 of
+        // the four axis neighbours (row index 0: r - 1, the source of upward populations)
+        V wx, ex_, sy, ny, swx, swy, sex, sey, nex, ney, nwx, nwy, tw, ts, te, tn;
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+            const int o = 32 * c;
+            const float2 w = mr.j[1][o - 1], e = mr.j[1][o + 1], sj = mr.j[0][o], nj = mr.j[2][o];
+            const float2 sw = mr.j[0][o - 1], se = mr.j[0][o + 1], ne = mr.j[2][o + 1], nw = mr.j[2][o - 1];
+            wx.set(c, w.x);
+            ex_.set(c, e.x);
+            sy.set(c, sj.y);
+            ny.set(c, nj.y);
+            swx.set(c, sw.x);
+            swy.set(c, sw.y);
+            sex.set(c, se.x);
+            sey.set(c, se.y);
+            nex.set(c, ne.x);
+            ney.set(c, ne.y);
+            nwx.set(c, nw.x);
+            nwy.set(c, nw.y);
+            tw.set(c, mr.T[1][o - 1]);
+            te.set(c, mr.T[1][o + 1]);
+            ts.set(c, mr.T[0][o]);
+            tn.set(c, mr.T[2][o]);
+        }
+        constexpr C a1 = C(3) * w9<C>(1), a2 = C(3) * w9<C>(5);
+        f[1] = vfma(V(a1), wx, f[1]);                    // e = (1, 0), from x - 1
+        f[3] = vfma(V(-a1), ex_, f[3]);                  // e = (-1, 0), from x + 1
+        f[2] = vfma(V(a1), sy, f[2]);                    // e = (0, 1), from r - 1
+        f[4] = vfma(V(-a1), ny, f[4]);                   // e = (0, -1), from r + 1
+        f[5] = vfma(V(a2), swx + swy, f[5]);             // e = (1, 1)
+        f[6] = vfma(V(a2), sey - sex, f[6]);             // e = (-1, 1)
+        f[7] = vfma(V(-a2), nex + ney, f[7]);            // e = (-1, -1)
+        f[8] = vfma(V(a2), nwx - nwy, f[8]);             // e = (1, -1)
+        const V T0(p.T0), h(p.hir0), q4(C(0.25));
+        g[0] = vfma(q4, tw, vfma((T0 + tw) * h, wx, g[0]));    // e = (1, 0)
+        g[1] = vfma(q4, ts, vfma((T0 + ts) * h, sy, g[1]));    // e = (0, 1)
+        g[2] = vfma(q4, te, vfma(-((T0 + te) * h), ex_, g[2]));  // e = (-1, 0)
+        g[3] = vfma(q4, tn, vfma(-((T0 + tn) * h), ny, g[3]));   // e = (0, -1)
     }
 }
 
-// rho u_r of the streamed populations in strip column col of a stage
+// rho u_r of the streamed populations in strip column lane + off of a stage
 template <class S, int NV, class C>
-__device__ __forceinline__ C stage_jr(const StepParams<C> &p, const S *stage, const MRows &mr, int col)
+__device__ __forceinline__ C stage_jr(const StepParams<C> &p, const S *stage, const MRows<NV> &mr, int lane, int off)
 {
-    return (spop<S, NV, C>(p, stage, mr, 2, col) - spop<S, NV, C>(p, stage, mr, 4, col)) +
-           (spop<S, NV, C>(p, stage, mr, 5, col) - spop<S, NV, C>(p, stage, mr, 8, col)) +
-           (spop<S, NV, C>(p, stage, mr, 6, col) - spop<S, NV, C>(p, stage, mr, 7, col));
+    return (spop<S, NV, C>(p, stage, mr, 2, lane, off) - spop<S, NV, C>(p, stage, mr, 4, lane, off)) +
+           (spop<S, NV, C>(p, stage, mr, 5, lane, off) - spop<S, NV, C>(p, stage, mr, 8, lane, off)) +
+           (spop<S, NV, C>(p, stage, mr, 6, lane, off) - spop<S, NV, C>(p, stage, mr, 7, lane, off));
 }
 
 // ---- the fused step kernel ------------------------------------------------------------
 // collide row j of the tile from its stage and write it (and its ghosts)
 template <class S, int NV, class C>
 __device__ __forceinline__ void collide_row(const StepParams<C> &p, const S *src, S *__restrict__ dst, const S *st,
-                                            const MRows &mr, int x0, int lane, int j, int64_t t,
+                                            const MRows<NV> &mr, int x0, int lane, int j, int64_t t,
                                             const Mom<Vec<C, NV>> &mp, const Mom<Vec<C, NV>> &mc,
                                             const Mom<Vec<C, NV>> &mn, const float2 *stab)
 {
@@ -1007,7 +1072,7 @@ __device__ __forceinline__ void collide_row(const StepParams<C> &p, const S *src
     V left, right;
     // rho u_r beside the strip, computed by every lane for its half's side
     // (lanes 0..15 the left, 16..31 the right) in one warp-uniform pass
-    const C beside = stage_jr<S, NV, C>(p, st, mr, lane < 16 ? -1 : 32 * NV);
+    const C beside = stage_jr<S, NV, C>(p, st, mr, lane, (lane < 16 ? -1 : 32 * NV) - lane);
 #pragma unroll
     for (int c = 0; c < NV; ++c) {
         const C up = __shfl_up_sync(0xffffffffu, mc.jr[c], 1);
@@ -1044,10 +1109,9 @@ __device__ __forceinline__ void collide_row(const StepParams<C> &p, const S *src
                 // the node's pre-collision moments, and every population as its deviation
                 // from the linear part at them
                 const C jx = mc.jx[c], jr = mc.jr[c], dT = mc.dT[c];
-                float *M = split_m(dst, p.plane);
-                M[o] = jx;
-                M[o + pl] = jr;
-                M[o + 2 * pl] = dT;
+                const MomRef M{split_m(dst, p.plane), p.plane};
+                M.j(o) = make_float2(jx, jr);
+                M.T(o) = dT;
 #pragma unroll
                 for (int k = 0; k < 9; ++k)
                     dst[o + k * pl] = store_as<S, C>(fo[k][c] - lin_part<C>(p, k, jx, jr, dT));
@@ -1119,9 +1183,11 @@ __device__ __forceinline__ void step_tile(const StepParams<C> &p, const S *__res
     // moment row m lives in slot (m - rlo + 1) % MSLOTS
     auto mslot = [&](int m) { return msm + ((m - rlo + 1) % MSLOTS) * MWin<NV>::SLOT; };
     auto mrows = [&](int r) {
-        MRows mr = {{nullptr, nullptr, nullptr}};
-        if constexpr (SPLIT)
-            mr = MRows{{mslot(r - 1), mslot(r), mslot(r + 1)}};
+        MRows<NV> mr = {};
+        if constexpr (SPLIT) {
+            const float *sl[3] = {mslot(r - 1), mslot(r), mslot(r + 1)};
+            mr = mrows_at<NV>(sl, lane);
+        }
         return mr;
     };
 
@@ -1644,10 +1710,9 @@ __global__ void split_state_in_kernel(S *buf, const double *f, const double *g, 
     }
     const float mx = float(jx), mr = float(jr), mT = float(dT);
     const int64_t o = (int64_t)(j + 1) * pitch + (i + PAD_COLS);
-    float *M = split_m(buf, plane);
-    M[o] = mx;
-    M[plane + o] = mr;
-    M[2 * plane + o] = mT;
+    const MomRef M{split_m(buf, plane), plane};
+    M.j(o) = make_float2(mx, mr);
+    M.T(o) = mT;
     for (int q = 0; q < 13; ++q)
         buf[(int64_t)q * plane + o] = store_as<S, float>(float(dev[q]) - lin_part<float>(lp, q, mx, mr, mT));
 }
@@ -1664,7 +1729,8 @@ __global__ void split_state_out_kernel(const S *buf, double *f, double *g, int n
     const StepParams<float> lp = lin_params(rho0, T0);
     const int64_t o = (int64_t)(j + 1) * pitch + (i + PAD_COLS);
     const float *M = split_m(buf, plane);
-    const float mx = M[o], mr = M[plane + o], mT = M[2 * plane + o];
+    const float2 jj = reinterpret_cast<const float2 *>(M)[o];
+    const float mx = jj.x, mr = jj.y, mT = M[2 * plane + o];
     for (int q = 0; q < 13; ++q) {
         const double v = double(lin_part<float>(lp, q, mx, mr, mT) + load_as<S, float>(buf + (int64_t)q * plane + o));
         if (q < 9)
