@@ -309,12 +309,12 @@ def error_vs_f64(works, storage: str, device, steps: int = 1000, sample: int = 4
             "steps": steps, "lattices": len(picks), **worst}
 
 
-def step_launches(lats, storage: str, launch, steps: int) -> int:
+def step_launches(lats, storage: str, launch, steps: int, strip: int = 0) -> int:
     """Kernels launched by `steps` steps.  One lattice runs its steps in persistent launches
     of up to 2^31 / (2 x warp tiles) steps each (either pattern).  A batch replays a
     captured launch of 64 steps and runs the rest in one launch; each launch is followed
     by the parameter advance."""
-    strip = 32 if storage == "f64" else 64
+    strip = strip or (32 if storage == "f64" else 64)
     band = launch[0]
     ntiles = sum(-(-lat.nx // strip) * -(-lat.nr // band) for lat in lats)
     per_launch = max(1, (1 << 31) // (2 * ntiles))
@@ -351,8 +351,11 @@ def run_gpu(args):
             target.step(n, graph=True, stream=stream)
     if args.autotune:  # outside the timed region; the lattices advance while tuning
         autotune.tune(target)
-    elif args.band or args.warps:
-        target.set_launch(max(args.band, 0), args.warps)
+    else:
+        if args.strip:
+            target.set_strip_width(args.strip)
+        if args.band or args.warps:
+            target.set_launch(max(args.band, 0), args.warps)
     if args.group > 0 and len(lats) == 1:
         target.set_item_group(args.group)
 
@@ -447,15 +450,15 @@ def run_gpu(args):
                             else "two population buffers")
                          + f" of {resident_mb(args.storage, args.pattern, nodes):.0f} MB)",
                    "bytes_per_lup": bpl,
-                   "launch": dict(zip(("band_rows", "warps_per_cta", "ctas" if len(lats) == 1 else "tiles"),
-                                      launch))},
+                   "launch": {**dict(zip(("band_rows", "warps_per_cta", "ctas" if len(lats) == 1 else "tiles"),
+                                         launch)), "strip_columns": target.strip_width}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                      "per": "step (the timed steps run in persistent launches of many steps)"},
         "cpu_baseline": cpu,
         "error": errors,
         "e2e": e2e,
-        "gpu_launches": step_launches(lats, args.storage, launch, args.steps),
+        "gpu_launches": step_launches(lats, args.storage, launch, args.steps, target.strip_width),
         "clocks": clk.summary(),
         "fields_finite": finite,
         "device_flags": flags,
@@ -753,6 +756,7 @@ def main(argv=None):
     ap.add_argument("--pattern", default="ab", choices=["ab", "aa"],
                     help="memory layout: two population buffers, or one updated in place (AA)")
     ap.add_argument("--band", type=int, default=0)
+    ap.add_argument("--strip", type=int, default=0, help="tile width in columns: 32 or 64 (0 = default)")
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--group", type=int, default=0,
                     help="one lattice: warp tiles per work item of the persistent launch (0 = automatic)")

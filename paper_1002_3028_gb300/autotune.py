@@ -1,11 +1,13 @@
-"""Autotuner of the step kernel's launch shape (band height x warps per CTA).
+"""Autotuner of the step kernel's launch and tile shape (strip width x band height x warps per CTA).
 
 Times each candidate shape on the live lattice or batch with CUDA events on
 its stream (after a warm-up), keeps the fastest, and remembers it in a small
 JSON cache keyed by the GPU name, the storage type and the lattice shape(s),
-so a later lattice of the same kind starts from the tuned shape.  Tuning
-steps the lattice: tune before setting the initial state, or save and
-restore it (``Lattice.get_state`` / ``set_state``).
+so a later lattice of the same kind starts from the tuned shape.  The tile
+is the warp's strip of 32 or 64 columns (one or two nodes per lane) by the
+band height; results are bit for bit the same for every shape.  Tuning steps
+the lattice: tune before setting the initial state, or save and restore it
+(``Lattice.save`` / ``restore``).
 """
 from __future__ import annotations
 
@@ -18,14 +20,17 @@ from typing import Iterable, List, Optional, Sequence, Tuple
 from . import build as _build
 
 CACHE = os.path.join(_build.BUILD, "autotune.json")
-# (band rows, warps per CTA).  One lattice: short bands keep many tiles between dependent
-# steps of the persistent launch; one-warp CTAs measured fastest.  A batch spreads each
-# step over many lattices and profits from longer bands.
-LATTICE_CANDIDATES: Tuple[Tuple[int, int], ...] = (
-    (1, 1), (2, 1), (3, 1), (4, 1), (5, 1), (6, 1), (7, 1), (8, 1), (6, 2),
+# (strip columns, band rows, warps per CTA).  One lattice: short bands keep many tiles between
+# dependent steps of the persistent launch; one-warp CTAs measured fastest; 32-column strips
+# double the tiles of small lattices.  A batch spreads each step over many lattices and
+# profits from longer bands.
+LATTICE_CANDIDATES: Tuple[Tuple[int, int, int], ...] = (
+    (64, 1, 1), (64, 2, 1), (64, 3, 1), (64, 4, 1), (64, 5, 1), (64, 6, 1), (64, 7, 1), (64, 8, 1), (64, 6, 2),
+    (32, 1, 1), (32, 2, 1), (32, 4, 1), (32, 6, 1), (32, 8, 1),
 )
-BATCH_CANDIDATES: Tuple[Tuple[int, int], ...] = (
-    (4, 1), (6, 1), (8, 1), (12, 1), (16, 1), (16, 2),
+BATCH_CANDIDATES: Tuple[Tuple[int, int, int], ...] = (
+    (64, 4, 1), (64, 6, 1), (64, 8, 1), (64, 12, 1), (64, 16, 1), (64, 16, 2),
+    (32, 8, 1), (32, 16, 1),
 )
 _lock = threading.Lock()
 
@@ -75,44 +80,63 @@ def _time(step_fn, steps: int, warmup: int) -> float:
     return e0.elapsed_time(e1) / steps
 
 
-def tune(target, candidates: Optional[Sequence[Tuple[int, int]]] = None, steps: int = 400, warmup: int = 20,
-         use_cache: bool = True) -> Tuple[int, int]:
-    """Pick and set the fastest (band rows, warps per CTA) for a Lattice or Batch.
+def _widths(storage: str, pattern: str) -> Tuple[int, ...]:
+    """Strip widths a lattice of this storage type and pattern accepts."""
+    if pattern == "aa":
+        return (32,) if storage == "f64" else (64,)
+    return (32,) if storage == "f64" else (64, 32)
+
+
+def _apply(target, cols: int, band: int, warps: int) -> None:
+    target.set_strip_width(cols)
+    target.set_launch(band, warps)
+
+
+def tune(target, candidates: Optional[Sequence[Tuple[int, int, int]]] = None, steps: int = 400,
+         warmup: int = 20, use_cache: bool = True) -> Tuple[int, int, int]:
+    """Pick and set the fastest (strip columns, band rows, warps per CTA) for a Lattice or Batch.
 
     Returns the chosen shape.  With use_cache, a shape tuned earlier for the
     same GPU, storage and lattice shapes is applied without timing.  Each
     candidate runs `steps` steps in one persistent launch (enough that the
-    launch's ramp and tail do not decide the ranking), twice.
+    launch's ramp and tail do not decide the ranking), twice.  Candidates
+    with a strip width the lattice does not accept are skipped.
     """
     from .lbm import Batch
 
     is_batch = isinstance(target, Batch)
-    shapes = [(m.nx, m.nr) for m in target.members] if is_batch else [(target.nx, target.nr)]
+    members = target.members if is_batch else [target]
+    shapes = [(m.nx, m.nr) for m in members]
+    pattern = members[0].pattern if members else "ab"
     key = lattice_key(target.storage, shapes)
     if use_cache:
         hit = _load().get(key)
         if hit:
-            target.set_launch(int(hit["band"]), int(hit["warps"]))
-            return int(hit["band"]), int(hit["warps"])
+            shape = (int(hit.get("strip", 0)), int(hit["band"]), int(hit["warps"]))
+            _apply(target, *shape)
+            return shape
     if is_batch:
         def run(n):
             target.step(n, graph=False)
     else:
         run = target.step
-    cands = list(candidates or (BATCH_CANDIDATES if is_batch else LATTICE_CANDIDATES))
+    widths = _widths(target.storage, pattern)
+    cands = [c for c in (candidates or (BATCH_CANDIDATES if is_batch else LATTICE_CANDIDATES)) if c[0] in widths]
+    if not cands:
+        raise ValueError(f"no candidate strip width among {widths} for {target.storage}/{pattern}")
     # bring the GPU to its working clocks first, then time every candidate twice, in
     # opposite orders, and keep each one's best: a fixed order would favour whichever
     # candidate runs last on a warming GPU
     run(max(warmup, steps))
     best = {}
     for order in (cands, cands[::-1]):
-        for band, warps in order:
-            target.set_launch(band, warps)
+        for shape in order:
+            _apply(target, *shape)
             ms = _time(run, steps, warmup)
-            best[(band, warps)] = min(ms, best.get((band, warps), ms))
-    results: List[Tuple[float, int, int]] = sorted((ms, b, w) for (b, w), ms in best.items())
-    ms, band, warps = results[0]
-    target.set_launch(band, warps)
-    _store(key, {"band": band, "warps": warps, "ms_per_step": ms,
-                 "timings": [[b, w, t] for t, b, w in results]})
-    return band, warps
+            best[shape] = min(ms, best.get(shape, ms))
+    results: List[Tuple[float, Tuple[int, int, int]]] = sorted((ms, sh) for sh, ms in best.items())
+    ms, shape = results[0]
+    _apply(target, *shape)
+    _store(key, {"strip": shape[0], "band": shape[1], "warps": shape[2], "ms_per_step": ms,
+                 "timings": [[*sh, t] for t, sh in results]})
+    return shape

@@ -120,9 +120,18 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 // moment-split storage: FP32 moment planes beside the 2-byte population planes
 bool is_split(int storage) { return storage == LBM_F16S || storage == LBM_BF16S; }
 
+
 // lattice columns per warp strip of the step kernel: 32 nodes per lane-slot,
 // two per lane in FP32 arithmetic
 int strip_cols(int storage) { return storage == LBM_F64 ? 32 : 64; }
+
+// nodes per lane of the two-buffer step kernels by default (strip width / 32)
+int default_nv(int storage) { return storage == LBM_F64 ? 1 : 2; }
+
+// ... and of a batch: moment-split batches default to 32-column strips (the ragged 256-jet
+// ensemble in FP16 moment-split storage: 721 against 832 us per step at 64 columns; the
+// rest-deviation FP16 batch is faster at 64, 377 against 392 us)
+int batch_default_nv(int storage) { return is_split(storage) ? 1 : default_nv(storage); }
 
 size_t storage_bytes(int storage)
 {
@@ -246,6 +255,7 @@ struct lbm_lattice {
     int ctas_max;          // CTAs resident on the device at once (persistent grid)
     int group;             // warp tiles per work item of lbm_step (0 = automatic)
     int device, sms;
+    int nv;                // nodes per lane of the two-buffer kernels: warp strips of 32 nv columns
     bool aa;               // AA pattern: one buffer (cur stays 0) and the tiles' edge moments
     int phase;             // AA pattern: representation of the stored state (lbm_aa.cuh)
     cudaEvent_t ready;     // recorded after the set-up work lbm_create enqueued
@@ -270,6 +280,7 @@ struct lbm_batch {
     bool far;          // a periodic member has a one-column last strip (lbm::far_wrap)
     int aa_ctas_min;   // AA: CTAs that cover the widest member's edge-wait distance
     int band, warps, band_eff;
+    int nv;        // nodes per lane: warp strips of 32 nv columns
     int sms;
     int ctas_max;  // CTAs resident on the device at once (persistent grid)
     cudaStream_t capture;  // private stream used to capture step graphs
@@ -299,7 +310,7 @@ lbm::StepParams<C> make_params(const lbm_lattice *h, const C *u_in, const C *T_i
     p.bc_bottom = d.bc_bottom;
     p.axisym = d.axisym ? 1 : 0;
     p.band = h->band_eff;
-    p.nstrips = (d.nx + strip_cols(d.storage) - 1) / strip_cols(d.storage);
+    p.nstrips = (d.nx + 32 * h->nv - 1) / (32 * h->nv);
     const int nbands = (d.nr + h->band_eff - 1) / h->band_eff;
     p.ntiles = p.nstrips * nbands;
     p.ntab = h->ntab;
@@ -363,19 +374,19 @@ int plan_launch(lbm_lattice *h)
     int per_sm = 0;
     cudaError_t e;
     switch (h->d.storage) {
-    case LBM_F64: e = h->aa ? lbm::occupancy_aa_run_f64(h->warps, &per_sm) : lbm::occupancy_run_f64(h->warps, &per_sm); break;
-    case LBM_F32: e = h->aa ? lbm::occupancy_aa_run_f32(h->warps, &per_sm) : lbm::occupancy_run_f32(h->warps, &per_sm); break;
-    case LBM_F16: e = h->aa ? lbm::occupancy_aa_run_f16(h->warps, &per_sm) : lbm::occupancy_run_f16(h->warps, &per_sm); break;
-    case LBM_F16S: e = lbm::occupancy_run_f16s(h->warps, &per_sm); break;
-    case LBM_BF16S: e = lbm::occupancy_run_bf16s(h->warps, &per_sm); break;
-    default: e = h->aa ? lbm::occupancy_aa_run_bf16(h->warps, &per_sm) : lbm::occupancy_run_bf16(h->warps, &per_sm); break;
+    case LBM_F64: e = h->aa ? lbm::occupancy_aa_run_f64(h->warps, &per_sm) : lbm::occupancy_run_f64(h->warps, h->nv, &per_sm); break;
+    case LBM_F32: e = h->aa ? lbm::occupancy_aa_run_f32(h->warps, &per_sm) : lbm::occupancy_run_f32(h->warps, h->nv, &per_sm); break;
+    case LBM_F16: e = h->aa ? lbm::occupancy_aa_run_f16(h->warps, &per_sm) : lbm::occupancy_run_f16(h->warps, h->nv, &per_sm); break;
+    case LBM_F16S: e = lbm::occupancy_run_f16s(h->warps, h->nv, &per_sm); break;
+    case LBM_BF16S: e = lbm::occupancy_run_bf16s(h->warps, h->nv, &per_sm); break;
+    default: e = h->aa ? lbm::occupancy_aa_run_bf16(h->warps, &per_sm) : lbm::occupancy_run_bf16(h->warps, h->nv, &per_sm); break;
     }
     if (e != cudaSuccess)
         return cuda_fail(e, "occupancy query");
     if (per_sm < 1)
         return fail(LBM_ERR_INVALID_ARG, "a CTA of %d warps does not fit on an SM", h->warps);
     const int resident_warps = per_sm * std::max(1, h->sms) * h->warps;
-    const int nstrips = (h->d.nx + strip_cols(h->d.storage) - 1) / strip_cols(h->d.storage);
+    const int nstrips = (h->d.nx + 32 * h->nv - 1) / (32 * h->nv);
     if (h->band > 0) {
         h->band_eff = h->band;
     } else {
@@ -407,7 +418,7 @@ struct AAPlan {
 AAPlan aa_plan(const lbm_lattice *h)
 {
     const lbm_desc &d = h->d;
-    const int nstrips = (d.nx + strip_cols(d.storage) - 1) / strip_cols(d.storage);
+    const int nstrips = (d.nx + 32 * h->nv - 1) / (32 * h->nv);
     const int64_t nbands = (d.nr + h->band_eff - 1) / h->band_eff;
     const int64_t resident = (int64_t)h->ctas_max * h->warps;
     AAPlan a;
@@ -541,12 +552,12 @@ int batch_occupancy(lbm_batch *b, int warps, int *per_sm)
 {
     cudaError_t e;
     switch (b->storage) {
-    case LBM_F64: e = b->aa ? lbm::occupancy_aa_batch_f64(warps, per_sm) : lbm::occupancy_batch_f64(warps, per_sm); break;
-    case LBM_F32: e = b->aa ? lbm::occupancy_aa_batch_f32(warps, per_sm) : lbm::occupancy_batch_f32(warps, per_sm); break;
-    case LBM_F16: e = b->aa ? lbm::occupancy_aa_batch_f16(warps, per_sm) : lbm::occupancy_batch_f16(warps, per_sm); break;
-    case LBM_F16S: e = lbm::occupancy_batch_f16s(warps, per_sm); break;
-    case LBM_BF16S: e = lbm::occupancy_batch_bf16s(warps, per_sm); break;
-    default: e = b->aa ? lbm::occupancy_aa_batch_bf16(warps, per_sm) : lbm::occupancy_batch_bf16(warps, per_sm); break;
+    case LBM_F64: e = b->aa ? lbm::occupancy_aa_batch_f64(warps, per_sm) : lbm::occupancy_batch_f64(warps, b->nv, per_sm); break;
+    case LBM_F32: e = b->aa ? lbm::occupancy_aa_batch_f32(warps, per_sm) : lbm::occupancy_batch_f32(warps, b->nv, per_sm); break;
+    case LBM_F16: e = b->aa ? lbm::occupancy_aa_batch_f16(warps, per_sm) : lbm::occupancy_batch_f16(warps, b->nv, per_sm); break;
+    case LBM_F16S: e = lbm::occupancy_batch_f16s(warps, b->nv, per_sm); break;
+    case LBM_BF16S: e = lbm::occupancy_batch_bf16s(warps, b->nv, per_sm); break;
+    default: e = b->aa ? lbm::occupancy_aa_batch_bf16(warps, per_sm) : lbm::occupancy_batch_bf16(warps, b->nv, per_sm); break;
     }
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "batch occupancy query");
 }
@@ -570,7 +581,7 @@ int batch_rebuild(lbm_batch *b, cudaStream_t s)
         return rc;
     if (per_sm < 1)
         return fail(LBM_ERR_INVALID_ARG, "a CTA of %d warps does not fit on an SM", b->warps);
-    const int cols = strip_cols(b->storage);
+    const int cols = 32 * b->nv;
     int64_t area = 0;  // strips x rows over all members
     for (lbm_lattice *h : b->members)
         area += (int64_t)((h->d.nx + cols - 1) / cols) * h->d.nr;
@@ -603,8 +614,9 @@ int batch_rebuild(lbm_batch *b, cudaStream_t s)
     std::vector<unsigned char> params(params_size(b->storage) * (size_t)std::max(1, n));
     for (int m = 0; m < n; ++m) {
         lbm_lattice *h = b->members[(size_t)m];
-        const int saved = h->band_eff;
+        const int saved = h->band_eff, saved_nv = h->nv;
         h->band_eff = b->band_eff;
+        h->nv = b->nv;
         if (b->storage == LBM_F64) {
             const auto p = params_d(h);
             std::memcpy(params.data() + (size_t)m * sizeof(p), &p, sizeof(p));
@@ -617,6 +629,7 @@ int batch_rebuild(lbm_batch *b, cudaStream_t s)
                 tiles.push_back({m, t});
         }
         h->band_eff = saved;
+        h->nv = saved_nv;
     }
     if (tiles.size() > (size_t)INT32_MAX)
         return fail(LBM_ERR_INVALID_ARG, "too many tiles in the batch");
@@ -703,22 +716,22 @@ cudaError_t batch_launch(lbm_batch *b, int nsteps, cudaStream_t s)
     switch (b->storage) {
     case LBM_F64:
         return lbm::launch_batch_f64(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<double> *>(b->d_params), n,
-                                     ctl, b->warps, ctas, b->far ? 1 : 0, s);
+                                     ctl, b->warps, ctas, b->far ? 1 : 0, b->nv, s);
     case LBM_F32:
         return lbm::launch_batch_f32(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params), n,
-                                     ctl, b->warps, ctas, b->far ? 1 : 0, s);
+                                     ctl, b->warps, ctas, b->far ? 1 : 0, b->nv, s);
     case LBM_F16:
         return lbm::launch_batch_f16(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params), n,
-                                     ctl, b->warps, ctas, b->far ? 1 : 0, s);
+                                     ctl, b->warps, ctas, b->far ? 1 : 0, b->nv, s);
     case LBM_F16S:
         return lbm::launch_batch_f16s(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params), n,
-                                      ctl, b->warps, ctas, b->far ? 1 : 0, s);
+                                      ctl, b->warps, ctas, b->far ? 1 : 0, b->nv, s);
     case LBM_BF16S:
         return lbm::launch_batch_bf16s(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params), n,
-                                       ctl, b->warps, ctas, b->far ? 1 : 0, s);
+                                       ctl, b->warps, ctas, b->far ? 1 : 0, b->nv, s);
     default:
         return lbm::launch_batch_bf16(b->d_tiles, b->ntiles, static_cast<lbm::StepParams<float> *>(b->d_params), n,
-                                      ctl, b->warps, ctas, b->far ? 1 : 0, s);
+                                      ctl, b->warps, ctas, b->far ? 1 : 0, b->nv, s);
     }
 }
 
@@ -873,6 +886,7 @@ int lbm_create(const lbm_desc *d, void *dev_mem, size_t bytes, lbm_lattice **out
     h->group = 0;
     h->aa = d->pattern == LBM_PATTERN_AA;
     h->phase = 0;
+    h->nv = default_nv(d->storage);
     cudaGetDevice(&h->device);
     h->sms = 1;
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -1044,7 +1058,7 @@ static int step_impl(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
         }
         return LBM_OK;
     }
-    const int nstrips = (d.nx + strip_cols(d.storage) - 1) / strip_cols(d.storage);
+    const int nstrips = (d.nx + 32 * h->nv - 1) / (32 * h->nv);
     const int64_t items = (int64_t)lbm::item_cols(nstrips, ctl.group) * ((d.nr + h->band_eff - 1) / h->band_eff);
     // steps per launch: the work counter stays below 2^31
     const int64_t per_launch = std::max<int64_t>(1, ((int64_t)1 << 31) / std::max<int64_t>(1, 2 * items));
@@ -1062,12 +1076,12 @@ static int step_impl(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
         ctl.nsteps = m;
         const int ctas = (int)std::min<int64_t>(h->ctas_max, (items + h->warps - 1) / h->warps);
         switch (d.storage) {
-        case LBM_F64: e = lbm::launch_run_f64(params_d(h), ctl, h->warps, ctas, s); break;
-        case LBM_F32: e = lbm::launch_run_f32(params_f(h), ctl, h->warps, ctas, s); break;
-        case LBM_F16: e = lbm::launch_run_f16(params_f(h), ctl, h->warps, ctas, s); break;
-        case LBM_F16S: e = lbm::launch_run_f16s(params_f(h), ctl, h->warps, ctas, s); break;
-        case LBM_BF16S: e = lbm::launch_run_bf16s(params_f(h), ctl, h->warps, ctas, s); break;
-        default: e = lbm::launch_run_bf16(params_f(h), ctl, h->warps, ctas, s); break;
+        case LBM_F64: e = lbm::launch_run_f64(params_d(h), ctl, h->warps, ctas, h->nv, s); break;
+        case LBM_F32: e = lbm::launch_run_f32(params_f(h), ctl, h->warps, ctas, h->nv, s); break;
+        case LBM_F16: e = lbm::launch_run_f16(params_f(h), ctl, h->warps, ctas, h->nv, s); break;
+        case LBM_F16S: e = lbm::launch_run_f16s(params_f(h), ctl, h->warps, ctas, h->nv, s); break;
+        case LBM_BF16S: e = lbm::launch_run_bf16s(params_f(h), ctl, h->warps, ctas, h->nv, s); break;
+        default: e = lbm::launch_run_bf16(params_f(h), ctl, h->warps, ctas, h->nv, s); break;
         }
         if (e != cudaSuccess)
             return cuda_fail(e, "step kernel launch");
@@ -1092,7 +1106,7 @@ int lbm_selftest_wait_timeout(lbm_lattice *h, int32_t *flags)
     const lbm_desc &d = h->d;
     lbm::RunCtl ctl;
     ctl.group = item_group(h);
-    const int nstrips = (d.nx + strip_cols(d.storage) - 1) / strip_cols(d.storage);
+    const int nstrips = (d.nx + 32 * h->nv - 1) / (32 * h->nv);
     const unsigned items = (unsigned)lbm::item_cols(nstrips, ctl.group) * (unsigned)((d.nr + h->band_eff - 1) / h->band_eff);
     unsigned *sync = h->at<unsigned>(h->L.off_sync);
     ctl.counter = sync;
@@ -1150,12 +1164,12 @@ int lbm_selftest_wait_timeout(lbm_lattice *h, int32_t *flags)
     if (e == cudaSuccess) {
         const int ctas = (int)std::min<int64_t>(h->ctas_max, ((int64_t)items + h->warps - 1) / h->warps);
         switch (d.storage) {
-        case LBM_F64: e = lbm::launch_run_f64(params_d(h), ctl, h->warps, ctas, s); break;
-        case LBM_F32: e = lbm::launch_run_f32(params_f(h), ctl, h->warps, ctas, s); break;
-        case LBM_F16: e = lbm::launch_run_f16(params_f(h), ctl, h->warps, ctas, s); break;
-        case LBM_F16S: e = lbm::launch_run_f16s(params_f(h), ctl, h->warps, ctas, s); break;
-        case LBM_BF16S: e = lbm::launch_run_bf16s(params_f(h), ctl, h->warps, ctas, s); break;
-        default: e = lbm::launch_run_bf16(params_f(h), ctl, h->warps, ctas, s); break;
+        case LBM_F64: e = lbm::launch_run_f64(params_d(h), ctl, h->warps, ctas, h->nv, s); break;
+        case LBM_F32: e = lbm::launch_run_f32(params_f(h), ctl, h->warps, ctas, h->nv, s); break;
+        case LBM_F16: e = lbm::launch_run_f16(params_f(h), ctl, h->warps, ctas, h->nv, s); break;
+        case LBM_F16S: e = lbm::launch_run_f16s(params_f(h), ctl, h->warps, ctas, h->nv, s); break;
+        case LBM_BF16S: e = lbm::launch_run_bf16s(params_f(h), ctl, h->warps, ctas, h->nv, s); break;
+        default: e = lbm::launch_run_bf16(params_f(h), ctl, h->warps, ctas, h->nv, s); break;
         }
     }
     if (e != cudaSuccess)
@@ -1385,6 +1399,44 @@ int lbm_set_launch(lbm_lattice *h, int32_t band_rows, int32_t warps_per_cta)
     return plan_launch(h);
 }
 
+// the strip width a lattice or batch of this storage type accepts: 0 (the default), or 32
+// columns (one node per lane) and, for FP32 arithmetic, 64 (two per lane); the AA pattern
+// keeps its default
+static int strip_nv(int storage, bool aa, int32_t cols, int *nv)
+{
+    if (cols == 0) {
+        *nv = default_nv(storage);
+        return LBM_OK;
+    }
+    if (aa && cols != 32 * default_nv(storage))
+        return fail(LBM_ERR_INVALID_ARG, "the AA pattern keeps strips of %d columns", 32 * default_nv(storage));
+    if (cols == 32 || (cols == 64 && storage != LBM_F64)) {
+        *nv = cols / 32;
+        return LBM_OK;
+    }
+    return fail(LBM_ERR_INVALID_ARG, "strip width %d: 0, 32%s", cols, storage == LBM_F64 ? "" : " or 64");
+}
+
+int lbm_set_strip_width(lbm_lattice *h, int32_t columns)
+{
+    if (!valid(h))
+        return fail(LBM_ERR_INVALID_ARG, "bad handle");
+    if (h->batch)
+        return fail(LBM_ERR_INVALID_ARG, "the lattice belongs to a batch: set the batch's strip width");
+    int nv = 0;
+    int rc = strip_nv(h->d.storage, h->aa, columns, &nv);
+    if (rc)
+        return rc;
+    const int old = h->nv;
+    h->nv = nv;
+    rc = plan_launch(h);
+    if (rc)
+        h->nv = old;
+    return rc;
+}
+
+int32_t lbm_get_strip_width(const lbm_lattice *h) { return valid(h) ? 32 * h->nv : -1; }
+
 int lbm_get_launch(const lbm_lattice *h, int32_t *band_rows, int32_t *warps_per_cta, int32_t *ctas)
 {
     if (!valid(h))
@@ -1409,6 +1461,7 @@ int lbm_batch_create(int32_t storage, lbm_batch **out)
     b->storage = storage;
     b->dirty = true;
     b->warps = 1;
+    b->nv = batch_default_nv(storage);
     int dev = 0;
     cudaGetDevice(&dev);
     b->sms = 1;
@@ -1455,6 +1508,8 @@ int lbm_batch_add(lbm_batch *b, lbm_lattice *h)
         return fail(LBM_ERR_INVALID_ARG, "storage type %d differs from the batch's %d", h->d.storage, b->storage);
     if (!b->members.empty() && b->members[0]->aa != h->aa)
         return fail(LBM_ERR_INVALID_ARG, "the members of a batch share one pattern");
+    if (h->aa && b->nv != default_nv(b->storage))
+        return fail(LBM_ERR_INVALID_ARG, "AA lattices join batches of the default strip width");
     b->members.push_back(h);
     h->batch = b;
     b->dirty = true;
@@ -1494,6 +1549,22 @@ int lbm_batch_set_launch(lbm_batch *b, int32_t band_rows, int32_t warps_per_cta)
     b->dirty = true;
     return LBM_OK;
 }
+
+int lbm_batch_set_strip_width(lbm_batch *b, int32_t columns)
+{
+    if (!b)
+        return fail(LBM_ERR_INVALID_ARG, "bad batch handle");
+    int nv = 0;
+    const bool aa = !b->members.empty() && b->members[0]->aa;
+    int rc = strip_nv(b->storage, aa, columns, &nv);
+    if (rc)
+        return rc;
+    b->nv = columns == 0 ? batch_default_nv(b->storage) : nv;
+    b->dirty = true;
+    return LBM_OK;
+}
+
+int32_t lbm_batch_get_strip_width(const lbm_batch *b) { return b ? 32 * b->nv : -1; }
 
 int lbm_batch_get_launch(const lbm_batch *b, int32_t *band_rows, int32_t *warps_per_cta, int32_t *tiles)
 {

@@ -15,11 +15,12 @@ namespace lbm {
 // returns the cudaError_t of the launch.
 #define LBM_DECLARE_LAUNCHERS(TAG, C)                                                                  \
     cudaError_t launch_run_##TAG(const StepParams<C> &p, const RunCtl &ctl, int warps_per_cta, int ctas,  \
-                                 cudaStream_t s);                                                      \
-    cudaError_t occupancy_run_##TAG(int warps_per_cta, int *ctas_per_sm);                              \
+                                 int nv, cudaStream_t s);                                              \
+    cudaError_t occupancy_run_##TAG(int warps_per_cta, int nv, int *ctas_per_sm);                      \
     cudaError_t launch_batch_##TAG(const TileRef *tiles, int ntiles, StepParams<C> *lattices, int nlat,     \
-                                   const RunCtl &ctl, int warps_per_cta, int ctas, int far, cudaStream_t s); \
-    cudaError_t occupancy_batch_##TAG(int warps_per_cta, int *ctas_per_sm);                            \
+                                   const RunCtl &ctl, int warps_per_cta, int ctas, int far, int nv,   \
+                                   cudaStream_t s);                                                    \
+    cudaError_t occupancy_batch_##TAG(int warps_per_cta, int nv, int *ctas_per_sm);                    \
     cudaError_t launch_fields_##TAG(const StepParams<C> &p, void *out, int out_f64, cudaStream_t s);   \
     cudaError_t launch_fill_##TAG(const StepParams<C> &p, cudaStream_t s);                             \
     cudaError_t launch_diag_##TAG(const StepParams<C> &p, int have_prev, double *partials, int nblocks,     \
@@ -43,11 +44,12 @@ namespace lbm {
 // the two-buffer launchers only (moment-split storage has no AA layout)
 #define LBM_DECLARE_AB_LAUNCHERS(TAG, C)                                                               \
     cudaError_t launch_run_##TAG(const StepParams<C> &p, const RunCtl &ctl, int warps_per_cta, int ctas,  \
-                                 cudaStream_t s);                                                      \
-    cudaError_t occupancy_run_##TAG(int warps_per_cta, int *ctas_per_sm);                              \
+                                 int nv, cudaStream_t s);                                              \
+    cudaError_t occupancy_run_##TAG(int warps_per_cta, int nv, int *ctas_per_sm);                      \
     cudaError_t launch_batch_##TAG(const TileRef *tiles, int ntiles, StepParams<C> *lattices, int nlat,     \
-                                   const RunCtl &ctl, int warps_per_cta, int ctas, int far, cudaStream_t s); \
-    cudaError_t occupancy_batch_##TAG(int warps_per_cta, int *ctas_per_sm);                            \
+                                   const RunCtl &ctl, int warps_per_cta, int ctas, int far, int nv,   \
+                                   cudaStream_t s);                                                    \
+    cudaError_t occupancy_batch_##TAG(int warps_per_cta, int nv, int *ctas_per_sm);                    \
     cudaError_t launch_fields_##TAG(const StepParams<C> &p, void *out, int out_f64, cudaStream_t s);   \
     cudaError_t launch_fill_##TAG(const StepParams<C> &p, cudaStream_t s);                             \
     cudaError_t launch_diag_##TAG(const StepParams<C> &p, int have_prev, double *partials, int nblocks,     \

@@ -260,11 +260,24 @@ struct Vec<C, 1> {
     __device__ __forceinline__ C operator[](int) const { return x; }
     __device__ __forceinline__ void set(int, C v) { x = v; }
 };
-template <class C> __device__ __forceinline__ Vec<C, 1> operator+(Vec<C, 1> a, Vec<C, 1> b) { return Vec<C, 1>(a.x + b.x); }
-template <class C> __device__ __forceinline__ Vec<C, 1> operator-(Vec<C, 1> a, Vec<C, 1> b) { return Vec<C, 1>(a.x - b.x); }
-template <class C> __device__ __forceinline__ Vec<C, 1> operator*(Vec<C, 1> a, Vec<C, 1> b) { return Vec<C, 1>(a.x * b.x); }
+// One rounding per operation, exactly as the paired instructions round each
+// of their two lanes: the compiler may not fuse a product into a following
+// sum across these operators (it would for plain a * b + c), so a node gives
+// the same bits at either strip width.
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <class C> __device__ __forceinline__ Vec<C, 1> operator+(Vec<C, 1> a, Vec<C, 1> b) { return Vec<C, 1>(rn_add(a.x, b.x)); }
+template <class C> __device__ __forceinline__ Vec<C, 1> operator-(Vec<C, 1> a, Vec<C, 1> b) { return Vec<C, 1>(rn_sub(a.x, b.x)); }
+template <class C> __device__ __forceinline__ Vec<C, 1> operator*(Vec<C, 1> a, Vec<C, 1> b) { return Vec<C, 1>(rn_mul(a.x, b.x)); }
 template <class C> __device__ __forceinline__ Vec<C, 1> operator-(Vec<C, 1> a) { return Vec<C, 1>(-a.x); }
-template <class C> __device__ __forceinline__ Vec<C, 1> vfma(Vec<C, 1> a, Vec<C, 1> b, Vec<C, 1> c) { return Vec<C, 1>(a.x * b.x + c.x); }
+template <class C> __device__ __forceinline__ Vec<C, 1> vfma(Vec<C, 1> a, Vec<C, 1> b, Vec<C, 1> c) { return Vec<C, 1>(rn_fma(a.x, b.x, c.x)); }
 
 template <>
 struct Vec<float, 2> {
@@ -749,7 +762,7 @@ __device__ __forceinline__ void collide(const StepParams<C> &p, const V (&f)[9],
     const V sx = F2x * V(sixth), sr = F2r * V(sixth);
     const V s1 = w1 * F1, s2 = w2 * F1;
     const V nomega = -omega;
-    fo[0] = vfma(nomega, fneq[0], f[0] + w0 * F1);
+    fo[0] = vfma(nomega, fneq[0], vfma(V(w0), F1, f[0]));  // one rounding at every strip width
     fo[1] = vfma(nomega, fneq[1], f[1] + (s1 + sx));
     fo[3] = vfma(nomega, fneq[3], f[3] + (s1 - sx));
     fo[2] = vfma(nomega, fneq[2], f[2] + (s1 + sr));
@@ -801,6 +814,13 @@ __device__ __forceinline__ C jr_beyond_outlet(const StepParams<C> &p, const S *s
 // column c of the strip (0 .. 32 NV - 1) reads population q at window index
 // c + H - e_qx.
 template <int NV> struct Stages { static constexpr int value = NV == 1 ? 4 : 3; };
+// the step kernels' ring: moment-split storage keeps three stages (populations one row
+// ahead, which its moment ring assumes) at every width
+template <class S, int NV>
+constexpr int step_stages()
+{
+    return IsSplit<S>::value ? 3 : Stages<NV>::value;
+}
 
 template <class S, int NV>
 struct Win {
@@ -1157,7 +1177,7 @@ __device__ __forceinline__ void step_tile(const StepParams<C> &p, const S *__res
 {
     using Wn = Win<S, NV>;
     using V = Vec<C, NV>;
-    constexpr int NSTAGE = Stages<NV>::value;
+    constexpr int NSTAGE = step_stages<S, NV>();
     constexpr int D = NSTAGE - 2;
     constexpr bool SPLIT = IsSplit<S>::value;
     constexpr bool ALT = std::is_same<S, float>::value;  // alternating band directions
@@ -1240,27 +1260,24 @@ __device__ __forceinline__ void step_tile(const StepParams<C> &p, const S *__res
     __syncwarp();
 }
 
-template <class S, class C>
-constexpr int step_smem_per_warp()
-{
-    constexpr int NV = NodesPerLane<C>::value;
-    return Stages<NV>::value * Win<S, NV>::STAGE * (int)sizeof(S) +
-           (IsSplit<S>::value ? MSLOTS * MWin<NV>::SLOT * (int)sizeof(float) : 0);
-}
-
-template <class S, class C>
+template <class S, class C, int NV = NodesPerLane<C>::value>
 constexpr int pop_ring_bytes()
 {
-    constexpr int NV = NodesPerLane<C>::value;
-    return Stages<NV>::value * Win<S, NV>::STAGE * (int)sizeof(S);
+    return step_stages<S, NV>() * Win<S, NV>::STAGE * (int)sizeof(S);
+}
+
+template <class S, class C, int NV = NodesPerLane<C>::value>
+constexpr int step_smem_per_warp()
+{
+    return pop_ring_bytes<S, C, NV>() + (IsSplit<S>::value ? MSLOTS * MWin<NV>::SLOT * (int)sizeof(float) : 0);
 }
 
 // shared memory of a step_run_kernel CTA: the warps' rings, then (2-byte
 // storage) the property table
-template <class S, class C>
+template <class S, class C, int NV = NodesPerLane<C>::value>
 constexpr int run_smem(int warps)
 {
-    return warps * step_smem_per_warp<S, C>() + (UseSmemTable<S, C>::value ? SMEM_TAB * (int)sizeof(float2) : 0);
+    return warps * step_smem_per_warp<S, C, NV>() + (UseSmemTable<S, C>::value ? SMEM_TAB * (int)sizeof(float2) : 0);
 }
 
 // ---- many steps of one lattice in one launch ----------------------------------------
@@ -1367,26 +1384,25 @@ __host__ __device__ constexpr bool far_wrap(int bc_in, int nx, int nstrips, int 
     return bc_in == IN_PERIODIC && (nx - 1) % strip_cols == 0 && nstrips >= 4;
 }
 
-template <class C>
+template <int NV, class C>
 __device__ __forceinline__ bool far_wrap(const StepParams<C> &p)
 {
-    return far_wrap(p.bc_in, p.nx, p.nstrips, 32 * NodesPerLane<C>::value);
+    return far_wrap(p.bc_in, p.nx, p.nstrips, 32 * NV);
 }
 
-template <class S, class C, bool FAR = false>
+template <class S, class C, bool FAR = false, int NV = NodesPerLane<C>::value>
 __global__ void __launch_bounds__(256) step_run_kernel(const __grid_constant__ StepParams<C> p, const RunCtl ctl)
 {
-    constexpr int NV = NodesPerLane<C>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    unsigned char *wbase = smem_raw + (size_t)warp * step_smem_per_warp<S, C>();
+    unsigned char *wbase = smem_raw + (size_t)warp * step_smem_per_warp<S, C, NV>();
     S *wsm = reinterpret_cast<S *>(wbase);
-    float *msm = IsSplit<S>::value ? reinterpret_cast<float *>(wbase + pop_ring_bytes<S, C>()) : nullptr;
+    float *msm = IsSplit<S>::value ? reinterpret_cast<float *>(wbase + pop_ring_bytes<S, C, NV>()) : nullptr;
     const float2 *stab = nullptr;
     if constexpr (UseSmemTable<S, C>::value) {
         if (p.ntab > 1 && p.ntab <= SMEM_TAB) {
-            float2 *tab = reinterpret_cast<float2 *>(smem_raw + (blockDim.x >> 5) * step_smem_per_warp<S, C>());
+            float2 *tab = reinterpret_cast<float2 *>(smem_raw + (blockDim.x >> 5) * step_smem_per_warp<S, C, NV>());
             load_smem_table(p, tab);
             __syncthreads();
             stab = tab;
@@ -1408,7 +1424,7 @@ __global__ void __launch_bounds__(256) step_run_kernel(const __grid_constant__ S
         const int item = (int)(n - (unsigned)k * items);
         const int b = item / cols, g = item - b * cols;
         if (k > 0 && !wait_neighbours<C>(p, ctl.flags, cols, ctl.radius, ctl.wrap != 0, b, g, k, ctl.spin_limit,
-                                         FAR && far_wrap(p))) {
+                                         FAR && far_wrap<NV>(p))) {
             if (lane == 0)
                 atomicOr(p.status, STATUS_TIMEOUT);
             break;  // whole warp
@@ -1439,11 +1455,10 @@ struct TileRef {
     int tile;     // warp tile index within that lattice
 };
 
-template <class S, class C, bool FAR = false>
+template <class S, class C, bool FAR = false, int NV = NodesPerLane<C>::value>
 __global__ void __launch_bounds__(256) batch_run_kernel(const TileRef *__restrict__ tiles, int ntiles,
                                                         const StepParams<C> *__restrict__ lattices, const RunCtl ctl)
 {
-    constexpr int NV = NodesPerLane<C>::value;
     constexpr int PW = (int)((sizeof(StepParams<C>) + 15) / 16);  // 16-byte words per parameter block
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -1451,9 +1466,9 @@ __global__ void __launch_bounds__(256) batch_run_kernel(const TileRef *__restric
     const int wpc = blockDim.x >> 5;
     // parameter blocks of all warps first, then the warps' staging rings
     StepParams<C> *pw = reinterpret_cast<StepParams<C> *>(smem_raw) + warp;
-    unsigned char *wbase = smem_raw + wpc * sizeof(StepParams<C>) + (size_t)warp * step_smem_per_warp<S, C>();
+    unsigned char *wbase = smem_raw + wpc * sizeof(StepParams<C>) + (size_t)warp * step_smem_per_warp<S, C, NV>();
     S *wsm = reinterpret_cast<S *>(wbase);
-    float *msm = IsSplit<S>::value ? reinterpret_cast<float *>(wbase + pop_ring_bytes<S, C>()) : nullptr;
+    float *msm = IsSplit<S>::value ? reinterpret_cast<float *>(wbase + pop_ring_bytes<S, C, NV>()) : nullptr;
     static_assert(sizeof(StepParams<C>) % 16 == 0 && PW <= 32, "parameter block copy");
     const unsigned total = (unsigned)ctl.nsteps * (unsigned)ntiles;
     unsigned n = 0;
@@ -1474,7 +1489,7 @@ __global__ void __launch_bounds__(256) batch_run_kernel(const TileRef *__restric
         const StepParams<C> &p = *pw;
         if (k > 0 && !wait_neighbours<C>(p, ctl.flags + (idx - t.tile), p.nstrips, ctl.radius, p.bc_in == IN_PERIODIC,
                                          t.tile / p.nstrips, t.tile % p.nstrips, k, ctl.spin_limit,
-                                         FAR && far_wrap(p))) {
+                                         FAR && far_wrap<NV>(p))) {
             if (lane == 0)
                 atomicOr(p.status, STATUS_TIMEOUT);
             break;  // whole warp
@@ -1487,10 +1502,10 @@ __global__ void __launch_bounds__(256) batch_run_kernel(const TileRef *__restric
     }
 }
 
-template <class S, class C>
+template <class S, class C, int NV = NodesPerLane<C>::value>
 constexpr int batch_smem_per_warp()
 {
-    return step_smem_per_warp<S, C>() + (int)sizeof(StepParams<C>);
+    return step_smem_per_warp<S, C, NV>() + (int)sizeof(StepParams<C>);
 }
 
 // after a batch launch of nsteps steps: every lattice counts the steps and,

@@ -4,4 +4,5 @@
 #define LBM_S bf16_s
 #define LBM_C float
 #define LBM_SPLIT 1
+#define LBM_MAX_NV 2  // widest strip: 32 LBM_MAX_NV columns
 #include "lbm_step_inst.cuh"

@@ -2,4 +2,5 @@
 #define LBM_TAG f64
 #define LBM_S double
 #define LBM_C double
+#define LBM_MAX_NV 1  // widest strip: 32 LBM_MAX_NV columns
 #include "lbm_step_inst.cuh"

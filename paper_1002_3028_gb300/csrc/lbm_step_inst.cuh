@@ -7,31 +7,45 @@
 
 namespace lbm {
 
-cudaError_t LBM_CAT(launch_run_, LBM_TAG)(const StepParams<LBM_C> &p, const RunCtl &ctl, int warps_per_cta, int ctas,
-                                          cudaStream_t s)
+// strip widths of the two-buffer step and batch kernels: 32 nv columns, nv nodes a lane
+// (FP32 arithmetic: 1 or 2; FP64: 1)
+template <int NV>
+static cudaError_t run_nv(const StepParams<LBM_C> &p, const RunCtl &ctl, int warps_per_cta, int ctas, cudaStream_t s)
 {
-    if (p.ntiles <= 0 || ctl.nsteps <= 0)
-        return cudaSuccess;
-    const int smem = run_smem<LBM_S, LBM_C>(warps_per_cta);
-    if (far_wrap(p.bc_in, p.nx, p.nstrips, 32 * NodesPerLane<LBM_C>::value))
-        step_run_kernel<LBM_S, LBM_C, true><<<ctas, 32 * warps_per_cta, smem, s>>>(p, ctl);
+    const int smem = run_smem<LBM_S, LBM_C, NV>(warps_per_cta);
+    if (far_wrap(p.bc_in, p.nx, p.nstrips, 32 * NV))
+        step_run_kernel<LBM_S, LBM_C, true, NV><<<ctas, 32 * warps_per_cta, smem, s>>>(p, ctl);
     else
-        step_run_kernel<LBM_S, LBM_C, false><<<ctas, 32 * warps_per_cta, smem, s>>>(p, ctl);
+        step_run_kernel<LBM_S, LBM_C, false, NV><<<ctas, 32 * warps_per_cta, smem, s>>>(p, ctl);
     return cudaGetLastError();
 }
 
-// allows the dynamic shared memory of the widest CTA and reports how many
-// CTAs of the given width fit on one SM (the fewer of the two instantiations)
-cudaError_t LBM_CAT(occupancy_run_, LBM_TAG)(int warps_per_cta, int *ctas_per_sm)
+cudaError_t LBM_CAT(launch_run_, LBM_TAG)(const StepParams<LBM_C> &p, const RunCtl &ctl, int warps_per_cta, int ctas,
+                                          int nv, cudaStream_t s)
+{
+    if (p.ntiles <= 0 || ctl.nsteps <= 0)
+        return cudaSuccess;
+#if LBM_MAX_NV > 1
+    if (nv == 2)
+        return run_nv<2>(p, ctl, warps_per_cta, ctas, s);
+#endif
+    return nv == 1 ? run_nv<1>(p, ctl, warps_per_cta, ctas, s) : cudaErrorInvalidValue;
+}
+
+// allows the dynamic shared memory of the widest CTA and reports how many CTAs of
+// the given width fit on one SM (the fewer of the two instantiations)
+template <int NV>
+static cudaError_t occupancy_run_nv(int warps_per_cta, int *ctas_per_sm)
 {
     int n[2] = {0, 0};
     for (int far = 0; far < 2; ++far) {
-        const void *fn = far ? reinterpret_cast<const void *>(step_run_kernel<LBM_S, LBM_C, true>)
-                             : reinterpret_cast<const void *>(step_run_kernel<LBM_S, LBM_C, false>);
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, run_smem<LBM_S, LBM_C>(8));
+        const void *fn = far ? reinterpret_cast<const void *>(step_run_kernel<LBM_S, LBM_C, true, NV>)
+                             : reinterpret_cast<const void *>(step_run_kernel<LBM_S, LBM_C, false, NV>);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             run_smem<LBM_S, LBM_C, NV>(8));
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[far], fn, 32 * warps_per_cta,
-                                                              run_smem<LBM_S, LBM_C>(warps_per_cta));
+                                                              run_smem<LBM_S, LBM_C, NV>(warps_per_cta));
         if (e != cudaSuccess)
             return e;
     }
@@ -39,41 +53,74 @@ cudaError_t LBM_CAT(occupancy_run_, LBM_TAG)(int warps_per_cta, int *ctas_per_sm
     return cudaSuccess;
 }
 
+cudaError_t LBM_CAT(occupancy_run_, LBM_TAG)(int warps_per_cta, int nv, int *ctas_per_sm)
+{
+#if LBM_MAX_NV > 1
+    if (nv == 2)
+        return occupancy_run_nv<2>(warps_per_cta, ctas_per_sm);
+#endif
+    return nv == 1 ? occupancy_run_nv<1>(warps_per_cta, ctas_per_sm) : cudaErrorInvalidValue;
+}
+
 // nsteps steps of every member lattice in one persistent launch, then the
 // device-side advance of the parameter table
+template <int NV>
+static cudaError_t batch_nv(const TileRef *tiles, int ntiles, StepParams<LBM_C> *lattices, const RunCtl &ctl,
+                            int warps_per_cta, int ctas, int far, cudaStream_t s)
+{
+    const int smem = warps_per_cta * batch_smem_per_warp<LBM_S, LBM_C, NV>();
+    if (far)
+        batch_run_kernel<LBM_S, LBM_C, true, NV><<<ctas, 32 * warps_per_cta, smem, s>>>(tiles, ntiles, lattices, ctl);
+    else
+        batch_run_kernel<LBM_S, LBM_C, false, NV><<<ctas, 32 * warps_per_cta, smem, s>>>(tiles, ntiles, lattices, ctl);
+    return cudaGetLastError();
+}
+
 cudaError_t LBM_CAT(launch_batch_, LBM_TAG)(const TileRef *tiles, int ntiles, StepParams<LBM_C> *lattices, int nlat,
-                                            const RunCtl &ctl, int warps_per_cta, int ctas, int far, cudaStream_t s)
+                                            const RunCtl &ctl, int warps_per_cta, int ctas, int far, int nv,
+                                            cudaStream_t s)
 {
     if (ntiles <= 0 || nlat <= 0 || ctl.nsteps <= 0)
         return cudaSuccess;
-    const int smem = warps_per_cta * batch_smem_per_warp<LBM_S, LBM_C>();
-    if (far)
-        batch_run_kernel<LBM_S, LBM_C, true><<<ctas, 32 * warps_per_cta, smem, s>>>(tiles, ntiles, lattices, ctl);
-    else
-        batch_run_kernel<LBM_S, LBM_C, false><<<ctas, 32 * warps_per_cta, smem, s>>>(tiles, ntiles, lattices, ctl);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaErrorInvalidValue;
+#if LBM_MAX_NV > 1
+    if (nv == 2)
+        e = batch_nv<2>(tiles, ntiles, lattices, ctl, warps_per_cta, ctas, far, s);
+#endif
+    if (nv == 1)
+        e = batch_nv<1>(tiles, ntiles, lattices, ctl, warps_per_cta, ctas, far, s);
     if (e != cudaSuccess)
         return e;
     advance_kernel<LBM_C><<<(nlat + 127) / 128, 128, 0, s>>>(lattices, nlat, ctl.nsteps);
     return cudaGetLastError();
 }
 
-cudaError_t LBM_CAT(occupancy_batch_, LBM_TAG)(int warps_per_cta, int *ctas_per_sm)
+template <int NV>
+static cudaError_t occupancy_batch_nv(int warps_per_cta, int *ctas_per_sm)
 {
     int n[2] = {0, 0};
     for (int far = 0; far < 2; ++far) {
-        const void *fn = far ? reinterpret_cast<const void *>(batch_run_kernel<LBM_S, LBM_C, true>)
-                             : reinterpret_cast<const void *>(batch_run_kernel<LBM_S, LBM_C, false>);
+        const void *fn = far ? reinterpret_cast<const void *>(batch_run_kernel<LBM_S, LBM_C, true, NV>)
+                             : reinterpret_cast<const void *>(batch_run_kernel<LBM_S, LBM_C, false, NV>);
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             8 * batch_smem_per_warp<LBM_S, LBM_C>());
+                                             8 * batch_smem_per_warp<LBM_S, LBM_C, NV>());
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[far], fn, 32 * warps_per_cta,
-                                                              warps_per_cta * batch_smem_per_warp<LBM_S, LBM_C>());
+                                                              warps_per_cta * batch_smem_per_warp<LBM_S, LBM_C, NV>());
         if (e != cudaSuccess)
             return e;
     }
     *ctas_per_sm = n[0] < n[1] ? n[0] : n[1];
     return cudaSuccess;
+}
+
+cudaError_t LBM_CAT(occupancy_batch_, LBM_TAG)(int warps_per_cta, int nv, int *ctas_per_sm)
+{
+#if LBM_MAX_NV > 1
+    if (nv == 2)
+        return occupancy_batch_nv<2>(warps_per_cta, ctas_per_sm);
+#endif
+    return nv == 1 ? occupancy_batch_nv<1>(warps_per_cta, ctas_per_sm) : cudaErrorInvalidValue;
 }
 
 cudaError_t LBM_CAT(launch_fields_, LBM_TAG)(const StepParams<LBM_C> &p, void *out, int out_f64, cudaStream_t s)

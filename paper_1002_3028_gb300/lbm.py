@@ -128,11 +128,18 @@ def lib(build: bool = True):
             L.lbm_batch_step.argtypes = [vp, i32, i32, vp]
             L.lbm_batch_set_launch.argtypes = [vp, i32, i32]
             L.lbm_batch_get_launch.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+            L.lbm_set_strip_width.argtypes = [vp, i32]
+            L.lbm_get_strip_width.restype = i32
+            L.lbm_get_strip_width.argtypes = [vp]
+            L.lbm_batch_set_strip_width.argtypes = [vp, i32]
+            L.lbm_batch_get_strip_width.restype = i32
+            L.lbm_batch_get_strip_width.argtypes = [vp]
             for name in ("lbm_required_bytes", "lbm_create", "lbm_set_inlet", "lbm_set_properties",
                          "lbm_step", "lbm_get_fields", "lbm_get_state", "lbm_set_state",
                          "lbm_set_launch", "lbm_get_launch", "lbm_check", "lbm_batch_create",
                          "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_set_launch",
-                         "lbm_batch_get_launch", "lbm_diagnostics", "lbm_diagnostics_noalloc"):
+                         "lbm_batch_get_launch", "lbm_diagnostics", "lbm_diagnostics_noalloc",
+                         "lbm_set_strip_width", "lbm_batch_set_strip_width"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -231,6 +238,14 @@ class Lattice:
     def set_launch(self, band_rows: int = 0, warps_per_cta: int = 0):
         """band_rows 0 = automatic (one wave of resident warps); warps 0 = unchanged."""
         _check(self._L.lbm_set_launch(self._h, band_rows, warps_per_cta), "lbm_set_launch")
+
+    def set_strip_width(self, columns: int = 0):
+        """Tile width of the step kernel in lattice columns: 32 or 64 (0 = the default)."""
+        _check(self._L.lbm_set_strip_width(self._h, int(columns)), "lbm_set_strip_width")
+
+    @property
+    def strip_width(self) -> int:
+        return int(self._L.lbm_get_strip_width(self._h))
 
     def selftest_wait_timeout(self) -> int:
         """Run a launch whose waits can never be met; returns the device status it raised."""
@@ -405,6 +420,13 @@ class Batch:
 
     def set_launch(self, band_rows: int = 0, warps_per_cta: int = 0):
         _check(self._L.lbm_batch_set_launch(self._h, band_rows, warps_per_cta), "lbm_batch_set_launch")
+
+    def set_strip_width(self, columns: int = 0):
+        _check(self._L.lbm_batch_set_strip_width(self._h, int(columns)), "lbm_batch_set_strip_width")
+
+    @property
+    def strip_width(self) -> int:
+        return int(self._L.lbm_batch_get_strip_width(self._h))
 
     def launch(self):
         """(band rows, warps per CTA, warp tiles per step) of the last rebuilt tables."""

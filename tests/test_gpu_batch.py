@@ -60,6 +60,25 @@ def test_batch_members_match_standalone(lbm, storage):
         assert states_equal(a, m)
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+def test_batch_with_32_column_strips_matches_standalone(lbm, storage):
+    """A batch stepped with 32-column tiles (one node per lane) advances every member exactly as
+    the member alone at the default tile."""
+    ws = ragged_jets(5, 9)
+    alone = [lbm.Lattice.from_workload(w, storage) for w in ws]
+    mixed = [lbm.Lattice.from_workload(w, storage) for w in ws]
+    b = lbm.Batch(storage)
+    b.set_strip_width(32)
+    for m in mixed:
+        b.add(m)
+    for a in alone:
+        a.step(23)
+    b.step(23, graph=True)
+    assert b.strip_width == 32
+    for a, m in zip(alone, mixed):
+        assert states_equal(a, m)
+
+
 def test_graph_replay_matches_eager(lbm):
     ws = ragged_jets(4, 5)
     eager = [lbm.Lattice.from_workload(w, "f16") for w in ws]

@@ -243,13 +243,19 @@ def test_f16s_jet_4096x1024_1000_steps_against_fp64(lbm):
     assert g.check() == 0
 
 
-@pytest.mark.parametrize("storage,band,warps", [("f32", 1, 1), ("f32", 3, 8), ("f32", 16, 4), ("f32", 64, 2),
-                                                ("f32", 1000, 4), ("f16s", 1, 1), ("f16s", 16, 4),
-                                                ("bf16s", 3, 8)])
-def test_launch_shape_does_not_change_results(lbm, orc, storage, band, warps):
+@pytest.mark.parametrize("storage,band,warps,strip", [
+    ("f32", 1, 1, 0), ("f32", 3, 8, 0), ("f32", 16, 4, 0), ("f32", 64, 2, 0), ("f32", 1000, 4, 0),
+    ("f16s", 1, 1, 0), ("f16s", 16, 4, 0), ("bf16s", 3, 8, 0),
+    ("f32", 1, 1, 32), ("f32", 6, 2, 32), ("f16", 4, 1, 32), ("bf16", 2, 4, 32), ("f16s", 5, 1, 32),
+    ("bf16s", 1, 2, 32),
+])
+def test_launch_shape_does_not_change_results(lbm, orc, storage, band, warps, strip):
+    """Band height, warps per CTA and the strip width (32-column tiles with one node per lane,
+    64 with two) leave every stored value unchanged."""
     w = workload(97, 40)
     ref = lbm.Lattice.from_workload(w, storage)
     alt = lbm.Lattice.from_workload(w, storage)
+    alt.set_strip_width(strip)
     alt.set_launch(band, warps)
     f0, g0 = I.random_state(97, 40, orc.feq(1.0, 0.0, 0.0), orc.geq(1.0, 0.0, 0.0), 0.03, 8)
     for lat in (ref, alt):
@@ -265,6 +271,7 @@ def test_launch_shape_does_not_change_results(lbm, orc, storage, band, warps):
     ("f16", "pipe", 4, 1), ("f64", "jet", 0, 1), ("f64", "annulus", 2, 1),
     ("f32", "jet", 0, 2), ("f32", "periodic_axis", 4, 2), ("f32", "open_periodic", 1, 3), ("f64", "jet", 3, 4),
     ("f16s", "pipe", 4, 1), ("f16s", "open_periodic", 1, 2), ("bf16s", "substrate", 0, 1),
+    ("f32/32", "periodic_axis", 1, 1), ("f32/32", "open_periodic", 4, 2), ("f16s/32", "jet", 2, 1),
 ])
 def test_many_steps_in_one_launch_equal_single_steps(lbm, orc, storage, bounds, band, group):
     """lbm_step(n) runs its n steps in one launch whose work items wait for their neighbours
@@ -272,10 +279,12 @@ def test_many_steps_in_one_launch_equal_single_steps(lbm, orc, storage, bounds, 
     (one-row bands depend on two bands each side; periodic ends make the first and last
     items neighbours; items of several strips, a ragged last one, or one item per band).
     The lattice spans several strips and bands with a ragged last strip."""
+    storage, _, strip = storage.partition("/")  # "f32/32": 32-column strips
     w = workload(150, 45, **BOUNDARIES[bounds])
     one = lbm.Lattice.from_workload(w, storage)
     many = lbm.Lattice.from_workload(w, storage)
     for lat in (one, many):
+        lat.set_strip_width(int(strip or 0))
         lat.set_launch(band, 1)
     many.set_item_group(group)
     assert many.item_group == group
