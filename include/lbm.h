@@ -228,9 +228,11 @@ LBM_API int lbm_diagnostics(lbm_lattice *h, lbm_diag *out, lbm_stream stream);
  * of this library.
  *   - Lattices of at most 16384 rows (nr); larger ones are refused with
  *     LBM_ERR_INVALID_ARG (use lbm_diagnostics for them).
- *   - The lattice's device must be current.  The first call on a device
- *     looks up the array's device address (no allocation); make that first
- *     call before any stream capture.
+ *   - The lattice's device must be current.  A call looks up the array's
+ *     device address (no allocation) unless its stream is capturing a
+ *     graph, when it takes the address of the device's last lookup: make
+ *     the first call on a device before any stream capture (a first call
+ *     inside a capture is refused with LBM_ERR_INVALID_ARG).
  *   - Every call on a device shares the array and overwrites the slots it
  *     uses (nothing needs to start at zero); calls whose work overlaps on
  *     the GPU, from any thread or stream, race on it.

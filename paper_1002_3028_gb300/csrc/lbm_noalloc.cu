@@ -25,13 +25,26 @@ static __device__ __align__(256) double g_scratch[kSlots];
 std::mutex g_mutex;
 double *g_scratch_ptr[kMaxDevices] = {};
 
-// device address of g_scratch on the current device (looked up once per device)
-int scratch_on(int device, double **ptr)
+// Device address of g_scratch on the current device.  It is looked up again
+// on every call whose stream is not capturing (a cheap query that allocates
+// nothing, so an address cached before a cudaDeviceReset is never reused);
+// a call made while its stream captures a graph takes the address of the
+// last lookup on the device, so the first call on a device must come before
+// any stream capture.
+int scratch_on(int device, cudaStream_t s, double **ptr)
 {
     if (device < 0 || device >= kMaxDevices)
         return api_fail(LBM_ERR_INVALID_ARG, "device index out of range for the fixed scratch table");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return api_fail(LBM_ERR_CUDA, "querying the stream's capture status failed");
+    }
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_ptr[device]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_scratch_ptr[device]) {
+        if (cap != cudaStreamCaptureStatusNone)
+            return api_fail(LBM_ERR_INVALID_ARG,
+                            "the first lbm_diagnostics_noalloc call on a device must come before any stream capture");
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess) {
@@ -92,11 +105,11 @@ extern "C" int lbm_diagnostics_noalloc(lbm_lattice *h, lbm_diag *out, lbm_stream
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev != v.device)
         return api_fail(LBM_ERR_INVALID_ARG, "make the lattice's device current before calling");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     double *scratch = nullptr;
-    rc = scratch_on(dev, &scratch);
+    rc = scratch_on(dev, s, &scratch);
     if (rc)
         return rc;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     rc = lattice_enter(h, s);
     if (rc)
         return rc;

@@ -45,18 +45,58 @@ def same(a, b, rel=1e-11):
             assert va == pytest.approx(vb, rel=rel, abs=1e-300), k
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
-def test_noalloc_equals_diagnostics_on_two_calls(lbm, storage):
+@pytest.mark.parametrize("storage,pattern", [("f64", "ab"), ("f32", "ab"), ("f16", "ab"), ("bf16", "ab"),
+                                             ("f16s", "ab"), ("bf16s", "ab"), ("f32", "aa"), ("bf16", "aa")])
+def test_noalloc_equals_diagnostics_on_two_calls(lbm, storage, pattern):
+    """Two calls in a row, at an odd and an even step count (the AA pattern's two
+    representations), equal lbm_diagnostics; an AA lattice keeps no previous state, so both
+    entry points report no residual for it."""
     w = I.jet_workload(nx=300, nr=70, R=20.0, ntab=64)
-    lat = lbm.Lattice.from_workload(w, storage)
+    lat = lbm.Lattice.from_workload(w, storage, pattern=pattern)
     L = lbm.lib()
     for n in range(2):
-        lat.step(25 + 7 * n)
+        lat.step(25 + 8 * n)  # 25, then 58 steps
         rc_a, a = call(lbm, L.lbm_diagnostics, lat)
         rc_b, b = call(lbm, L.lbm_diagnostics_noalloc, lat)
         assert rc_a == rc_b == 0
         same(b, a)
-        assert b["mass"] > 0 and not math.isnan(b["residual_max"])
+        assert b["mass"] > 0 and math.isnan(b["residual_max"]) == (pattern == "aa")
+    lat.close()
+
+
+def test_noalloc_allocates_nothing_and_leaves_the_lattice_memory_alone(lbm):
+    """After a first call, further calls change neither the free device memory nor the
+    caching allocator's reserved bytes, and no byte of the lattice's own device block
+    (its populations, tables, counters and scratch area) is written."""
+    w = I.jet_workload(nx=300, nr=70, R=20.0, ntab=64)
+    lat = lbm.Lattice.from_workload(w, "f32")
+    lat.step(30)
+    L = lbm.lib()
+    assert call(lbm, L.lbm_diagnostics_noalloc, lat)[0] == 0
+    block0 = lat._mem.clone()  # the lattice's whole device block, as the library laid it out
+    torch.cuda.synchronize()
+    free, reserved = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    for _ in range(3):
+        rc, d = call(lbm, L.lbm_diagnostics_noalloc, lat)
+        assert rc == 0 and d["mass"] > 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free
+    assert torch.cuda.memory_reserved() == reserved
+    assert torch.equal(lat._mem, block0)
+    lat.close()
+
+
+def test_noalloc_takes_the_largest_lattice_its_array_holds(lbm):
+    cfg = I.LatticeConfig(nx=2, nr=16384, bc_in="periodic", bc_out="periodic", bc_top="wall", T_top=1.0)
+    lat = lbm.Lattice(cfg, "f32")
+    f0, g0 = I.random_state(2, 16384, [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4, [0.25] * 4, 0.02, 5)
+    lat.set_state(f0, g0, 0)
+    lat.step(3)
+    L = lbm.lib()
+    rc_a, a = call(lbm, L.lbm_diagnostics, lat)
+    rc_b, b = call(lbm, L.lbm_diagnostics_noalloc, lat)
+    assert rc_a == rc_b == 0
+    same(b, a)
     lat.close()
 
 
