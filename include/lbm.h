@@ -157,12 +157,19 @@ LBM_API int lbm_required_bytes(const lbm_desc *d, size_t *bytes);
  *             cudaMalloc (and later free) its own.  Caller memory must
  *             outlive the handle.
  *   out:      receives the handle; untouched on error.
- * Synchronises the current device.  Errors: INVALID_ARG, OOM, CUDA.
+ * The set-up (zeroing, tables, ghost cells; a stream-ordered allocation of
+ * the library's own memory) is queued on the legacy default stream and the
+ * host does not wait for it: every later call orders its stream after the
+ * set-up's completion event.  Caller memory must be free of other work
+ * queued on non-blocking streams when the call is made.
+ * Errors: INVALID_ARG, OOM, CUDA.
  */
 LBM_API int lbm_create(const lbm_desc *d, void *dev_mem, size_t bytes, lbm_lattice **out);
 
-/* Release the handle (and the library's own memory, after synchronising
- * the device).  NULL is a no-op. */
+/* Release the handle.  The library's own memory is freed in stream order
+ * after the last work queued through the handle, without waiting on the
+ * host; caller memory may be reused once that work has run.  NULL is a
+ * no-op. */
 LBM_API void lbm_destroy(lbm_lattice *h);
 
 /*

@@ -157,10 +157,13 @@ def required_bytes(cfg: LatticeConfig, storage: str = "f32", pattern: str = "ab"
     return int(n.value)
 
 
-def _stream_ptr(stream) -> C.c_void_p:
+def _stream_ptr(stream, *users) -> C.c_void_p:
+    """The stream's handle; the lattices in `users` note the stream for their ``close``."""
     import torch
 
     s = stream if stream is not None else torch.cuda.current_stream()
+    for u in users:
+        u._used_on(s)
     return C.c_void_p(int(s.cuda_stream))
 
 
@@ -192,9 +195,15 @@ class Lattice:
         self._L = lib()
         self._desc = make_desc(cfg, storage, pattern)
         self.nbytes = required_bytes(cfg, storage, pattern)
+        self._streams = {}
         with torch.cuda.device(self.device):
-            # the caching allocator hands out 512-byte aligned blocks
+            # the caching allocator hands out 512-byte aligned blocks, in the order of the
+            # current stream; the library's set-up runs on the default stream, so that
+            # stream first waits for the work the block's previous owner queued
             self._mem = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+            self._alloc_stream = torch.cuda.current_stream(self.device)
+            if self._alloc_stream != torch.cuda.default_stream(self.device):
+                torch.cuda.default_stream(self.device).wait_stream(self._alloc_stream)
             h = C.c_void_p()
             _check(self._L.lbm_create(C.byref(self._desc), C.c_void_p(self._mem.data_ptr()),
                                       self.nbytes, C.byref(h)), "lbm_create")
@@ -211,7 +220,16 @@ class Lattice:
         if getattr(self, "_h", None):
             self._L.lbm_destroy(self._h)
             self._h = None
+            # work queued on other streams may still use the block: the caching allocator
+            # hands it out again only after that work
+            for s in self._streams.values():
+                self._mem.record_stream(s)
+            self._streams = {}
             self._mem = None
+
+    def _used_on(self, s):
+        if s != self._alloc_stream:
+            self._streams.setdefault(s.cuda_stream, s)
 
     def __del__(self):
         try:
@@ -226,14 +244,14 @@ class Lattice:
     def set_inlet(self, u_in, T_in, stream=None):
         u = np.ascontiguousarray(u_in, dtype=np.float64)
         T = np.ascontiguousarray(T_in, dtype=np.float64)
-        _check(self._L.lbm_set_inlet(self._h, _dptr(u), _dptr(T), len(u), _stream_ptr(stream)),
+        _check(self._L.lbm_set_inlet(self._h, _dptr(u), _dptr(T), len(u), _stream_ptr(stream, self)),
                "lbm_set_inlet")
 
     def set_properties(self, nu, alpha, T_lo, T_hi, stream=None):
         a = np.ascontiguousarray(nu, dtype=np.float64)
         b = np.ascontiguousarray(alpha, dtype=np.float64)
         _check(self._L.lbm_set_properties(self._h, _dptr(a), _dptr(b), len(a), float(T_lo),
-                                          float(T_hi), _stream_ptr(stream)), "lbm_set_properties")
+                                          float(T_hi), _stream_ptr(stream, self)), "lbm_set_properties")
 
     def set_launch(self, band_rows: int = 0, warps_per_cta: int = 0):
         """band_rows 0 = automatic (one wave of resident warps); warps 0 = unchanged."""
@@ -268,7 +286,7 @@ class Lattice:
         return b.value, w.value, c.value
 
     def step(self, n: int = 1, stream=None):
-        _check(self._L.lbm_step(self._h, int(n), _stream_ptr(stream)), "lbm_step")
+        _check(self._L.lbm_step(self._h, int(n), _stream_ptr(stream, self)), "lbm_step")
 
     def diagnostics(self, stream=None) -> dict:
         """FP64 mass, heat, max speed, steady residual and non-finite count (synchronises).
@@ -277,7 +295,7 @@ class Lattice:
         density or a non-finite velocity or temperature.
         """
         d = Diag()
-        rc = self._L.lbm_diagnostics(self._h, C.byref(d), _stream_ptr(stream))
+        rc = self._L.lbm_diagnostics(self._h, C.byref(d), _stream_ptr(stream, self))
         if rc not in (LBM_OK, -4):
             _check(rc, "lbm_diagnostics")
         out = d.as_dict()
@@ -304,7 +322,7 @@ class Lattice:
         code = 0 if out.dtype == torch.float64 else 1
         if out.dtype not in (torch.float64, torch.float32) or not out.is_contiguous():
             raise ValueError("fields output must be a contiguous float64/float32 tensor")
-        _check(self._L.lbm_get_fields(self._h, C.c_void_p(out.data_ptr()), code, _stream_ptr(stream)),
+        _check(self._L.lbm_get_fields(self._h, C.c_void_p(out.data_ptr()), code, _stream_ptr(stream, self)),
                "lbm_get_fields")
         return out
 
@@ -315,7 +333,7 @@ class Lattice:
         f = torch.empty((9, self.nr, self.nx), dtype=torch.float64, device=self.device)
         g = torch.empty((4, self.nr, self.nx), dtype=torch.float64, device=self.device)
         _check(self._L.lbm_get_state(self._h, C.c_void_p(f.data_ptr()), C.c_void_p(g.data_ptr()),
-                                     _stream_ptr(stream)), "lbm_get_state")
+                                     _stream_ptr(stream, self)), "lbm_get_state")
         return f, g
 
     def set_state(self, f, g, step: int = 0, stream=None):
@@ -326,7 +344,7 @@ class Lattice:
         if tuple(f.shape) != (9, self.nr, self.nx) or tuple(g.shape) != (4, self.nr, self.nx):
             raise ValueError("state shapes must be (9, nr, nx) and (4, nr, nx)")
         _check(self._L.lbm_set_state(self._h, C.c_void_p(f.data_ptr()), C.c_void_p(g.data_ptr()),
-                                     int(step), _stream_ptr(stream)), "lbm_set_state")
+                                     int(step), _stream_ptr(stream, self)), "lbm_set_state")
         # keep the inputs alive until the conversion kernel has run
         torch.cuda.current_stream(self.device).synchronize() if stream is None else stream.synchronize()
 
@@ -348,7 +366,7 @@ class Lattice:
         shape, dt = self._checkpoint_shape()
         out = torch.empty(shape, dtype=dt, device=self.device)
         assert out.numel() * out.element_size() == n.value
-        _check(self._L.lbm_save(self._h, C.c_void_p(out.data_ptr()), _stream_ptr(stream)), "lbm_save")
+        _check(self._L.lbm_save(self._h, C.c_void_p(out.data_ptr()), _stream_ptr(stream, self)), "lbm_save")
         return out, self.step_count
 
     def restore(self, planes, step: int, stream=None):
@@ -362,7 +380,7 @@ class Lattice:
                 planes.numel() * planes.element_size() != n.value:
             raise ValueError("checkpoint does not match this lattice")
         planes = planes.to(self.device).contiguous()
-        _check(self._L.lbm_restore(self._h, C.c_void_p(planes.data_ptr()), int(step), _stream_ptr(stream)),
+        _check(self._L.lbm_restore(self._h, C.c_void_p(planes.data_ptr()), int(step), _stream_ptr(stream, self)),
                "lbm_restore")
         # keep the input alive until the copies have run
         torch.cuda.current_stream(self.device).synchronize() if stream is None else stream.synchronize()
@@ -375,7 +393,7 @@ class Lattice:
         if (planes.numel() * planes.element_size() != n.value
                 or planes.device != self.device or not planes.is_contiguous()):
             raise ValueError("checkpoint does not match this lattice (a contiguous device tensor)")
-        _check(self._L.lbm_restore(self._h, C.c_void_p(planes.data_ptr()), int(step), _stream_ptr(stream)),
+        _check(self._L.lbm_restore(self._h, C.c_void_p(planes.data_ptr()), int(step), _stream_ptr(stream, self)),
                "lbm_restore")
 
 
@@ -416,7 +434,8 @@ class Batch:
         self.members = [m for m in self.members if m is not lat]
 
     def step(self, n: int = 1, graph: bool = True, stream=None):
-        _check(self._L.lbm_batch_step(self._h, int(n), int(bool(graph)), _stream_ptr(stream)), "lbm_batch_step")
+        _check(self._L.lbm_batch_step(self._h, int(n), int(bool(graph)), _stream_ptr(stream, *self.members)),
+               "lbm_batch_step")
 
     def set_launch(self, band_rows: int = 0, warps_per_cta: int = 0):
         _check(self._L.lbm_batch_set_launch(self._h, band_rows, warps_per_cta), "lbm_batch_set_launch")

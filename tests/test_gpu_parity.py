@@ -413,3 +413,40 @@ def test_state_roundtrip_through_fp64_resumes_closely(lbm, storage):
     fa, ga = a.get_state()
     fb, gb = b.get_state()
     assert (fa - fb).abs().max().item() < tol and (ga - gb).abs().max().item() < tol
+
+
+def test_create_refuses_caller_memory_too_small_or_misaligned(lbm):
+    """lbm_create with a caller block one byte short (LBM_ERR_OOM) or off the 256-byte
+    alignment (LBM_ERR_INVALID_ARG) fails before any device work and leaves *out untouched."""
+    import ctypes as C
+
+    w = workload(70, 20)
+    d = lbm.make_desc(w.cfg, "f32", "ab")
+    need = lbm.required_bytes(w.cfg, "f32")
+    mem = torch.empty(need + 512, dtype=torch.uint8, device="cuda")
+    L = lbm.lib()
+    for ptr, nbytes, rc in ((mem.data_ptr(), need - 1, -2), (mem.data_ptr() + 128, need, -1)):
+        h = C.c_void_p(12345)
+        assert L.lbm_create(C.byref(d), C.c_void_p(ptr), nbytes, C.byref(h)) == rc
+        assert h.value == 12345
+    h = C.c_void_p()
+    assert L.lbm_create(C.byref(d), C.c_void_p(mem.data_ptr()), need, C.byref(h)) == 0
+    L.lbm_destroy(h)
+
+
+def test_side_stream_steps_equal_default_stream_steps(lbm):
+    """A lattice stepped and read on a side stream gives the default stream's results; the
+    binding keeps its block from reuse until that stream's work has run."""
+    w = workload(97, 40)
+    a = lbm.Lattice.from_workload(w, "f32")
+    b = lbm.Lattice.from_workload(w, "f32")
+    a.step(30)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.step(30, stream=s)
+        Fb = b.fields(stream=s)
+    s.synchronize()
+    assert torch.equal(a.fields(), Fb)
+    assert list(b._streams) == [s.cuda_stream]
+    b.close()
+    a.close()
