@@ -260,6 +260,11 @@ struct lbm_lattice {
     int phase;             // AA pattern: representation of the stored state (lbm_aa.cuh)
     cudaEvent_t ready;     // recorded after the set-up work lbm_create enqueued
     cudaEvent_t last;      // recorded after the last work enqueued on the lattice
+    // counters of the two-buffer persistent launch, carried from launch to launch
+    // (lbm::RunCtl): valid for sync_items work items; 0 = reset before the next launch
+    int64_t sync_items;
+    unsigned sync_cbase, sync_fbase;
+    bool sync_captured;    // a launch was captured into a graph: reset before every launch
 
     void *buf(int b) const { return mem + L.off_buf[b]; }
     template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(mem + off); }
@@ -390,9 +395,11 @@ int plan_launch(lbm_lattice *h)
     if (h->band > 0) {
         h->band_eff = h->band;
     } else {
-        // tenths of a round (AA: 3.4 for every storage type; band 8 on the 4096 x 1024 jet,
-        // the fastest of bands 4..16 measured for FP32 and FP16)
-        const int64_t rounds10 = storage_bytes(h->d.storage) == 2 || h->aa ? 34 : 54;
+        // tenths of a round between dependent items, by storage type (AA: 3.4 for every
+        // type).  On the 4096 x 1024 jet, of bands 4..16: FP32 band 5 (5.4 rounds; band 6
+        // runs a launch at either 79 or 87 us per step), FP16 band 8, moment-split band 7
+        // (95 us per step against 97 at band 6 and 103 at band 8)
+        const int64_t rounds10 = h->aa ? 34 : (is_split(h->d.storage) ? 40 : (storage_bytes(h->d.storage) == 2 ? 34 : 54));
         const int64_t want_tiles = std::max<int64_t>(1, rounds10 * resident_warps / 10);
         const int64_t band = ((int64_t)h->d.nr * nstrips + want_tiles - 1) / want_tiles;
         h->band_eff = (int)std::min<int64_t>(8, std::max<int64_t>(1, band));
@@ -887,6 +894,9 @@ int lbm_create(const lbm_desc *d, void *dev_mem, size_t bytes, lbm_lattice **out
     h->aa = d->pattern == LBM_PATTERN_AA;
     h->phase = 0;
     h->nv = default_nv(d->storage);
+    h->sync_items = 0;
+    h->sync_cbase = h->sync_fbase = 0;
+    h->sync_captured = false;
     cudaGetDevice(&h->device);
     h->sms = 1;
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -1068,12 +1078,28 @@ static int step_impl(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
     ctl.radius = h->band_eff >= 2 ? 1 : 2;
     ctl.wrap = d.bc_in == LBM_IN_PERIODIC ? 1 : 0;
     ctl.spin_limit = lbm::RUN_SPIN_LIMIT;
+    // The counters carry on from the previous launch (RunCtl) unless the item
+    // count changed, a wait ran out (lbm_check) or the launch goes into a graph,
+    // whose replays must each start from a reset.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "querying the stream");
+    if (cap != cudaStreamCaptureStatusNone)
+        h->sync_captured = true;
     for (int64_t done = 0; done < nsteps;) {
         const int m = (int)std::min<int64_t>(per_launch, nsteps - done);
-        cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)4 * (size_t)(1 + items), s);
-        if (e != cudaSuccess)
-            return cuda_fail(e, "work counter reset");
+        cudaError_t e = cudaSuccess;
+        if (h->sync_items != items || h->sync_captured) {
+            e = cudaMemsetAsync(sync, 0, (size_t)4 * (size_t)(1 + items), s);
+            if (e != cudaSuccess)
+                return cuda_fail(e, "work counter reset");
+            h->sync_items = items;
+            h->sync_cbase = h->sync_fbase = 0;
+        }
         ctl.nsteps = m;
+        ctl.cbase = h->sync_cbase;
+        ctl.fbase = h->sync_fbase;
+        ctl.first = 0;
         const int ctas = (int)std::min<int64_t>(h->ctas_max, (items + h->warps - 1) / h->warps);
         switch (d.storage) {
         case LBM_F64: e = lbm::launch_run_f64(params_d(h), ctl, h->warps, ctas, h->nv, s); break;
@@ -1083,8 +1109,12 @@ static int step_impl(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
         case LBM_BF16S: e = lbm::launch_run_bf16s(params_f(h), ctl, h->warps, ctas, h->nv, s); break;
         default: e = lbm::launch_run_bf16(params_f(h), ctl, h->warps, ctas, h->nv, s); break;
         }
-        if (e != cudaSuccess)
+        if (e != cudaSuccess) {
+            h->sync_items = 0;
             return cuda_fail(e, "step kernel launch");
+        }
+        h->sync_cbase += (unsigned)m * (unsigned)items + (unsigned)ctas * (unsigned)h->warps;
+        h->sync_fbase += 32u * (unsigned)(m - 1);
         h->cur ^= (m & 1);
         h->step += m;
         h->prev_valid = true;
@@ -1156,11 +1186,11 @@ int lbm_selftest_wait_timeout(lbm_lattice *h, int32_t *flags)
         *flags = first & second;  // LBM_STATUS_TIMEOUT only if both waits gave up
         return LBM_OK;
     }
-    // every counter at zero and the work counter past sub-step 0: each item
+    // every counter at zero and the first item past sub-step 0: each item
     // taken belongs to sub-step 1 and waits for a sub-step that never runs
+    h->sync_items = 0;  // the next lbm_step starts from a reset
+    ctl.first = items;
     cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)4 * (size_t)(1 + items), s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(sync, &items, sizeof(unsigned), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         const int ctas = (int)std::min<int64_t>(h->ctas_max, ((int64_t)items + h->warps - 1) / h->warps);
         switch (d.storage) {
@@ -1229,6 +1259,8 @@ int lbm_check(lbm_lattice *h, int32_t *flags)
         e = cudaMemset(h->mem + h->L.off_status, 0, sizeof(int));
     if (e != cudaSuccess)
         return cuda_fail(e, "reading the status word");
+    if (v & lbm::STATUS_TIMEOUT)
+        h->sync_items = 0;  // a launch stopped early: its counters are not where the host expects
     *flags = v;
     return LBM_OK;
 }

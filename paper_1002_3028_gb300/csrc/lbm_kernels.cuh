@@ -1304,13 +1304,21 @@ constexpr int STATUS_TIMEOUT = 1;
 constexpr int RUN_SPIN_LIMIT = 1 << 21;  // polls of at most ~2 us: a few seconds
 
 struct RunCtl {
-    unsigned *counter;  // work items taken (zeroed before the launch)
-    unsigned *flags;    // per work item: 32 x sub-steps done (zeroed before the launch)
+    unsigned *counter;  // work items taken (zeroed before the launch; step_run_kernel: at cbase)
+    unsigned *flags;    // per work item: 32 x sub-steps done (zeroed before the launch; step_run_kernel: at fbase)
     int nsteps;         // sub-steps of this launch
     int radius;         // neighbour bands an item depends on
     int wrap;           // strips wrap around (periodic axial ends; a batch reads each lattice's ends)
     int group;          // G: warp tiles (adjacent strips of one band) per work item
     int spin_limit;     // polls before a wait gives up (RUN_SPIN_LIMIT; smaller in the self-test)
+    // step_run_kernel only.  Its counters carry on from launch to launch: the work
+    // counter ends a launch advanced by exactly nsteps x items + the grid's warps
+    // (below), and every item's completion counter by 32 (nsteps - 1), since nothing
+    // in a launch waits for its last sub-step.  The host tracks both, so consecutive
+    // launches need no reset between them.
+    unsigned cbase = 0;  // the work counter's value at the start of the launch
+    unsigned fbase = 0;  // every completion counter's value at the start of the launch
+    unsigned first = 0;  // the first work item of the launch (0; the self-test starts at sub-step 1)
 };
 
 // work items per band of a lattice with nstrips strips
@@ -1329,14 +1337,15 @@ __device__ __forceinline__ void red_release_add(unsigned *a, unsigned v)
 }
 
 // Every lane waits until the items around item (band b, column g) of a
-// lattice (its counters start at `flags`, `cols` items per band) have
+// lattice (its counters start at `flags`, `cols` items per band, each at
+// `base` before sub-step 0) have
 // finished sub-step k - 1: radius bands and one item column on each side,
 // and also the items two columns out when `far`.  Returns false if the
 // wait runs out or another warp's wait ran out (the status word is read
 // only while waiting).
 template <class C>
 __device__ bool wait_neighbours(const StepParams<C> &p, const unsigned *flags, int cols, int radius, bool wrap, int b,
-                                int g, int k, int spin_limit, bool far = false)
+                                int g, int k, int spin_limit, bool far = false, unsigned base = 0)
 {
     // lane l < 3 (2 radius + 1) watches neighbour (band b + l / 3 - radius, column g + l % 3 - 1);
     // when far, lane 16 + m < 16 + 2 (2 radius + 1) watches (band b + m / 2 - radius, column g -+ 2)
@@ -1357,7 +1366,7 @@ __device__ bool wait_neighbours(const StepParams<C> &p, const unsigned *flags, i
         if (bb >= 0 && bb < nbands && gg >= 0 && gg < cols)
             f = flags + bb * cols + gg;
     }
-    const unsigned want = 32u * (unsigned)k;
+    const unsigned want = base + 32u * (unsigned)k;
     for (int it = 0;; ++it) {
         const bool ok = f == nullptr || (int)(ld_acquire(f) - want) >= 0;
         if (__all_sync(0xffffffffu, ok)) {
@@ -1411,20 +1420,25 @@ __global__ void __launch_bounds__(256) step_run_kernel(const __grid_constant__ S
     const int cols = item_cols(p.nstrips, ctl.group);
     const unsigned items = (unsigned)cols * (unsigned)((p.nr + p.band - 1) / p.band);
     const unsigned total = (unsigned)ctl.nsteps * items;
+    // Every warp draws from the counter once, then once per item it runs (its
+    // last draw is past the end), so the counter ends the launch at
+    // cbase + total + the grid's warps.  (Handing each warp its first item by
+    // its index instead put the 4096 x 1024 jet into a steady schedule 8%
+    // slower: which warps meet which items first shapes the whole launch.)
     unsigned n = 0;
     if (lane == 0)
-        n = atomicAdd(ctl.counter, 1u);
+        n = ctl.first + (atomicAdd(ctl.counter, 1u) - ctl.cbase);
     n = __shfl_sync(0xffffffffu, n, 0);
     while (n < total) {
         // take the next item now: its latency hides behind this one
         unsigned next = 0;
         if (lane == 0)
-            next = atomicAdd(ctl.counter, 1u);
+            next = ctl.first + (atomicAdd(ctl.counter, 1u) - ctl.cbase);
         const int k = (int)(n / items);
         const int item = (int)(n - (unsigned)k * items);
         const int b = item / cols, g = item - b * cols;
         if (k > 0 && !wait_neighbours<C>(p, ctl.flags, cols, ctl.radius, ctl.wrap != 0, b, g, k, ctl.spin_limit,
-                                         FAR && far_wrap<NV>(p))) {
+                                         FAR && far_wrap<NV>(p), ctl.fbase)) {
             if (lane == 0)
                 atomicOr(p.status, STATUS_TIMEOUT);
             break;  // whole warp
@@ -1434,7 +1448,8 @@ __global__ void __launch_bounds__(256) step_run_kernel(const __grid_constant__ S
         const int s1 = min((g + 1) * ctl.group, p.nstrips);
         for (int s = g * ctl.group; s < s1; ++s)
             step_tile<S, NV, C>(p, src, dst, wsm, b * p.nstrips + s, lane, p.step + k, stab, msm);
-        red_release_add(ctl.flags + item, 1u);
+        if (k + 1 < ctl.nsteps)  // no item of this launch waits for the last sub-step
+            red_release_add(ctl.flags + item, 1u);
         n = __shfl_sync(0xffffffffu, next, 0);
     }
 }
