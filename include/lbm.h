@@ -318,7 +318,7 @@ LBM_API int lbm_restore(lbm_lattice *h, const void *dev_in, int64_t step, lbm_st
  * warp per tile of a strip of columns (lbm_set_strip_width) x band_rows rows.
  * band_rows >= 1 fixes the band height; 0 lets the library choose it from
  * the number of warps the GPU holds at once (the default).
- * warps_per_cta == 0 keeps the current value (default 2).  Results do not
+ * warps_per_cta == 0 keeps the current value (default 1).  Results do not
  * depend on the launch shape.
  */
 LBM_API int lbm_set_launch(lbm_lattice *h, int32_t band_rows, int32_t warps_per_cta);

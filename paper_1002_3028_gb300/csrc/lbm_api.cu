@@ -395,14 +395,17 @@ int plan_launch(lbm_lattice *h)
     if (h->band > 0) {
         h->band_eff = h->band;
     } else {
-        // tenths of a round between dependent items, by storage type (AA: 3.4 for every
-        // type).  On the 4096 x 1024 jet, of bands 4..16: FP32 band 5 (5.4 rounds; band 6
-        // runs a launch at either 79 or 87 us per step), FP16 band 8, moment-split band 7
-        // (95 us per step against 97 at band 6 and 103 at band 8)
-        const int64_t rounds10 = h->aa ? 34 : (is_split(h->d.storage) ? 40 : (storage_bytes(h->d.storage) == 2 ? 34 : 54));
+        // tenths of a round between dependent items (AA: 3.4 for every storage type).  On
+        // the 4096 x 1024 jet, of bands 4..16: FP32 band 5 (5.4 rounds; band 6 runs a launch
+        // at either 79 or 87 us per step); 2-byte storage 4.0 rounds: rest-deviation FP16
+        // band 7 (65.1 us per step against 66.5 at band 6 and 69.0 at band 8), moment-split
+        // band 9 of its 12 warps per SM (89.8 us every launch; band 10 ran 88.8 with some
+        // launches at 90-95, band 8 91.3 and band 11 108)
+        const bool split = is_split(h->d.storage) && !h->aa;
+        const int64_t rounds10 = h->aa ? 34 : (storage_bytes(h->d.storage) == 2 ? 40 : 54);
         const int64_t want_tiles = std::max<int64_t>(1, rounds10 * resident_warps / 10);
         const int64_t band = ((int64_t)h->d.nr * nstrips + want_tiles - 1) / want_tiles;
-        h->band_eff = (int)std::min<int64_t>(8, std::max<int64_t>(1, band));
+        h->band_eff = (int)std::min<int64_t>(split ? 10 : 8, std::max<int64_t>(1, band));
     }
     if (h->aa)  // the edge area holds the edge rows of bands of at least AA_BAND_MIN rows
         h->band_eff = std::max(h->band_eff, std::min(lbm::AA_BAND_MIN, h->d.nr));

@@ -254,7 +254,7 @@ class Lattice:
                                           float(T_hi), _stream_ptr(stream, self)), "lbm_set_properties")
 
     def set_launch(self, band_rows: int = 0, warps_per_cta: int = 0):
-        """band_rows 0 = automatic (one wave of resident warps); warps 0 = unchanged."""
+        """band_rows 0 = automatic (a few rounds of resident warps between dependent tiles); warps 0 = unchanged."""
         _check(self._L.lbm_set_launch(self._h, band_rows, warps_per_cta), "lbm_set_launch")
 
     def set_strip_width(self, columns: int = 0):
