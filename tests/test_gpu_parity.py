@@ -450,3 +450,33 @@ def test_side_stream_steps_equal_default_stream_steps(lbm):
     assert list(b._streams) == [s.cuda_stream]
     b.close()
     a.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+def test_counters_carried_across_launches_with_shape_changes(lbm, orc, storage):
+    """lbm_step's work and completion counters carry on from one launch to the next and are
+    reset only when the item count changes or a wait ran out.  Launches of 1..7 steps with the
+    band, the strip width and the item group changed between some of them (and repeated
+    between others), and the bounded-wait self-test in the middle, give the bits of one
+    lattice stepped in a single launch."""
+    w = workload(150, 45, **BOUNDARIES["open_periodic"])
+    ref = lbm.Lattice.from_workload(w, storage)
+    lat = lbm.Lattice.from_workload(w, storage)
+    f0, g0 = I.random_state(150, 45, orc.feq(1.0, 0.02, 0.0), orc.geq(1.2, 0.02, 0.0), 0.05, 31)
+    for x in (ref, lat):
+        x.set_state(f0, g0, 0)
+    plan = [(3, 0, 0, 0), (1, 0, 0, 0), (4, 0, 0, 0), (2, 4, 0, 0), (5, 4, 0, 0), (7, 1, 32, 0),
+            (1, 1, 32, 0), (2, 2, 32, 2), (3, 0, 64, 0), (6, 0, 64, 3), (2, 0, 0, 0)]
+    steps = 0
+    for n, band, strip, group in plan:
+        lat.set_strip_width(strip)
+        lat.set_launch(band, 1)
+        lat.set_item_group(group)
+        lat.step(n)
+        steps += n
+        if steps == 15:  # a timed-out launch leaves the counters to be reset
+            assert lat.selftest_wait_timeout() != 0 and lat.step_count == 15
+    ref.step(steps)
+    assert lat.step_count == ref.step_count == steps
+    assert torch.equal(lat.save()[0], ref.save()[0])
+    assert lat.check() == 0 and ref.check() == 0
