@@ -1,7 +1,8 @@
 """Autotuner of the step kernel's launch and tile shape (strip width x band height x warps per CTA).
 
 Times each candidate shape on the live lattice or batch with CUDA events on
-its stream (after a warm-up), keeps the fastest, and remembers it in a small
+its stream (after a warm-up), three runs each, keeps the one whose slowest
+run is fastest, and remembers it in a small
 JSON cache keyed by the GPU name, the storage type and the lattice shape(s),
 so a later lattice of the same kind starts from the tuned shape.  The tile
 is the warp's strip of 32 or 64 columns (one or two nodes per lane) by the
@@ -25,12 +26,12 @@ CACHE = os.path.join(_build.BUILD, "autotune.json")
 # double the tiles of small lattices.  A batch spreads each step over many lattices and
 # profits from longer bands.
 LATTICE_CANDIDATES: Tuple[Tuple[int, int, int], ...] = (
-    (64, 1, 1), (64, 2, 1), (64, 3, 1), (64, 4, 1), (64, 5, 1), (64, 6, 1), (64, 7, 1), (64, 8, 1), (64, 6, 2),
-    (32, 1, 1), (32, 2, 1), (32, 4, 1), (32, 6, 1), (32, 8, 1),
+    (64, 1, 1), (64, 2, 1), (64, 3, 1), (64, 4, 1), (64, 5, 1), (64, 6, 1), (64, 7, 1), (64, 8, 1), (64, 9, 1),
+    (64, 10, 1), (64, 6, 2), (32, 1, 1), (32, 2, 1), (32, 4, 1), (32, 6, 1), (32, 8, 1),
 )
 BATCH_CANDIDATES: Tuple[Tuple[int, int, int], ...] = (
-    (64, 4, 1), (64, 6, 1), (64, 8, 1), (64, 12, 1), (64, 16, 1), (64, 16, 2),
-    (32, 8, 1), (32, 16, 1),
+    (64, 4, 1), (64, 8, 1), (64, 12, 1), (64, 16, 1), (64, 16, 2), (64, 32, 1),
+    (32, 8, 1), (32, 16, 1), (32, 32, 1), (32, 64, 1),
 )
 _lock = threading.Lock()
 
@@ -99,8 +100,9 @@ def tune(target, candidates: Optional[Sequence[Tuple[int, int, int]]] = None, st
     Returns the chosen shape.  With use_cache, a shape tuned earlier for the
     same GPU, storage and lattice shapes is applied without timing.  Each
     candidate runs `steps` steps in one persistent launch (enough that the
-    launch's ramp and tail do not decide the ranking), twice.  Candidates
-    with a strip width the lattice does not accept are skipped.
+    launch's ramp and tail do not decide the ranking), three times, and is
+    ranked by its slowest run.  Candidates with a strip width the lattice
+    does not accept are skipped.
     """
     from .lbm import Batch
 
@@ -124,17 +126,19 @@ def tune(target, candidates: Optional[Sequence[Tuple[int, int, int]]] = None, st
     cands = [c for c in (candidates or (BATCH_CANDIDATES if is_batch else LATTICE_CANDIDATES)) if c[0] in widths]
     if not cands:
         raise ValueError(f"no candidate strip width among {widths} for {target.storage}/{pattern}")
-    # bring the GPU to its working clocks first, then time every candidate twice, in
-    # opposite orders, and keep each one's best: a fixed order would favour whichever
-    # candidate runs last on a warming GPU
+    # bring the GPU to its working clocks first, then time every candidate three times, in
+    # alternating orders (a fixed order would favour whichever candidate runs last on a
+    # warming GPU), and rank each by its slowest run: a shape whose launches fall into a
+    # slower schedule part of the time (FP32 band 6 on the 4096 x 1024 jet runs a launch
+    # at either 79 or 87 us per step) must not win on its fast launches
     run(max(warmup, steps))
-    best = {}
-    for order in (cands, cands[::-1]):
+    worst = {}
+    for order in (cands, cands[::-1], cands):
         for shape in order:
             _apply(target, *shape)
             ms = _time(run, steps, warmup)
-            best[shape] = min(ms, best.get(shape, ms))
-    results: List[Tuple[float, Tuple[int, int, int]]] = sorted((ms, sh) for sh, ms in best.items())
+            worst[shape] = max(ms, worst.get(shape, ms))
+    results: List[Tuple[float, Tuple[int, int, int]]] = sorted((ms, sh) for sh, ms in worst.items())
     ms, shape = results[0]
     _apply(target, *shape)
     _store(key, {"strip": shape[0], "band": shape[1], "warps": shape[2], "ms_per_step": ms,

@@ -598,12 +598,16 @@ int batch_rebuild(lbm_batch *b, cudaStream_t s)
     if (b->band > 0) {
         b->band_eff = b->band;
     } else {
-        // as for one lattice (plan_launch), up to 16 rows: a batch's tiles of one step are
-        // spread over many lattices, and longer bands halve the halo cost of small ones
+        // as for one lattice (plan_launch), up to a cap by storage type: a batch's tiles of
+        // one step are spread over many lattices, and longer bands cut the halo cost of small
+        // ones.  The ragged 256-jet ensemble, us per step: FP32 438.8 at band 16 (441.6 at
+        // 12, 445.9 at 24); rest-deviation FP16 369.3 at 32 (376.9 at 16, 385.5 at 64);
+        // moment-split FP16 585.9 at 64 (648.0 at 16, 603.6 at 96, 667.2 at 128)
         const int64_t rounds10 = storage_bytes(b->storage) == 2 ? 34 : 45;
         const int64_t want_tiles = std::max<int64_t>(1, rounds10 * (int64_t)per_sm * std::max(1, b->sms) * b->warps / 10);
         const int64_t band = (area + want_tiles - 1) / want_tiles;
-        b->band_eff = (int)std::min<int64_t>(16, std::max<int64_t>(1, band));
+        const int64_t cap = b->aa ? 16 : (is_split(b->storage) ? 64 : (storage_bytes(b->storage) == 2 ? 32 : 16));
+        b->band_eff = (int)std::min<int64_t>(cap, std::max<int64_t>(1, band));
     }
     if (b->aa)  // the members' edge areas hold bands of at least AA_BAND_MIN rows
         b->band_eff = std::max(b->band_eff, lbm::AA_BAND_MIN);

@@ -29,7 +29,7 @@ def test_tune_applies_and_caches_a_candidate(lbm, tmp_path, monkeypatch):
     shape = autotune.tune(lat, candidates=cands, steps=60, warmup=5)
     assert shape in cands
     assert (lat.strip_width, *lat.launch()[:2]) == shape
-    assert lat.step_count == 60 + 2 * 2 * 65  # tuning steps the lattice: a warm-up, then each candidate twice
+    assert lat.step_count == 60 + 3 * 2 * 65  # tuning steps the lattice: a warm-up, then each candidate three times
     data = json.load(open(autotune.CACHE))
     (entry,) = data.values()
     assert (entry["strip"], entry["band"], entry["warps"]) == shape and len(entry["timings"]) == 2
