@@ -7,10 +7,13 @@
 // values: row -1 (ghost), rows 0..nr-1, row nr (ghost); in every row the
 // lattice column i sits at element i + PAD_COLS, so columns -1 and nx are
 // ghosts and every warp's strip starts on an aligned boundary.  Every value
-// is the deviation from the rest state, f_k - w_k rho0 and g_k - T0/4.  The
-// arithmetic type C is double for FP64 storage and float for FP32/FP16/BF16;
-// all collision arithmetic runs on deviations, so the rounding of a stored
-// value is relative to its (small) departure from rest.
+// is the deviation from the rest state, f_k - w_k rho0 and g_k - T0/4 (the
+// moment-split 2-byte types store FP32 moments beside the planes and each
+// value as its deviation from the part of the equilibrium linear in them;
+// see "moment-split storage").  The arithmetic type C is double for FP64
+// storage and float for the others; all collision arithmetic runs on
+// deviations, so the rounding of a stored value is relative to its (small)
+// departure from rest.
 //
 // Boundaries as ghosts.  The boundary rules only ever pick, for a pulled
 // source outside the lattice, a value computed from the post-collision
@@ -22,9 +25,10 @@
 // one, exactly as in the rules' definition.
 //
 // Work split of the step kernel.  One warp owns a strip of 32 NV consecutive
-// columns (NV = 2 nodes per lane in FP32 arithmetic, at columns x0 + lane and
-// x0 + 32 + lane, computed together with the paired FP32x2 instructions;
-// NV = 1 in FP64) and marches up a band of rows.  The populations each row
+// columns (NV = 2 nodes per lane, at columns x0 + lane and x0 + 32 + lane,
+// computed together with the paired FP32x2 instructions, or NV = 1: a launch
+// parameter in FP32 arithmetic; NV = 1 in FP64) and marches along a band of
+// rows (FP32 storage: up in even bands, down in odd ones).  The populations each row
 // pulls are staged in the warp's shared-memory ring by asynchronous copies
 // issued one row ahead (two in FP64); from a landed row the warp forms the
 // Eq. 2 moments and collides the row below, whose radial neighbours' moments
