@@ -154,11 +154,14 @@ def serve(requests: List[Request], engine: Engine, budget_bytes: float, chunk: i
 class GpuBatchEngine(Engine):
     """All active lattices in one liblbm batch (persistent multi-step launches, graph replay).
 
-    ``pattern="aa"`` keeps every lattice in one population buffer updated in place, so the
-    same memory budget admits more lattices (FP16: about 32 instead of 52 bytes per node).
+    The default storage is FP16 moment-split ("f16s"), the 2-byte type that stays within
+    1e-3 of FP64 on u and T over whole runs.  ``pattern="aa"`` keeps every lattice in one
+    population buffer updated in place, so the same memory budget admits more lattices
+    (rest-deviation FP16: about 32 instead of 52 bytes per node; moment-split storage has no
+    AA form).
     """
 
-    def __init__(self, storage: str = "f16", device=None, graph: bool = True, pattern: str = "ab"):
+    def __init__(self, storage: str = "f16s", device=None, graph: bool = True, pattern: str = "ab"):
         import torch
 
         from . import lbm
