@@ -1,4 +1,5 @@
-"""Whole-jet checks of the paper's qualitative results on the GPU path (FP32 storage).
+"""Whole-jet checks of the paper's qualitative results on the GPU path (FP32 storage, and FP16
+moment-split storage for the free jet).
 
 Section 4 of the paper reports that the radial temperature distribution of
 the jet is Gaussian at successive cross-sections (Fig. 6), with the jet
@@ -40,11 +41,11 @@ def gaussian_fit(r, y):
     return A, s, r2
 
 
-@pytest.mark.parametrize("bc_out", ["outflow", "wall"])
-def test_developed_jet_has_gaussian_radial_temperature(lbm, bc_out):
+@pytest.mark.parametrize("bc_out,storage", [("outflow", "f32"), ("wall", "f32"), ("outflow", "f16s")])
+def test_developed_jet_has_gaussian_radial_temperature(lbm, bc_out, storage):
     w = I.jet_workload(nx=1024, nr=256)
     w = dataclasses.replace(w, cfg=dataclasses.replace(w.cfg, bc_out=bc_out))
-    lat = lbm.Lattice.from_workload(w, "f32")
+    lat = lbm.Lattice.from_workload(w, storage)
     lat.step(30000)
     assert lat.check() == 0
     F = lat.fields().cpu().numpy()
