@@ -1089,7 +1089,7 @@ static int step_impl(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
     }
     const int nstrips = (d.nx + 32 * h->nv - 1) / (32 * h->nv);
     const int64_t items = (int64_t)lbm::item_cols(nstrips, ctl.group) * ((d.nr + h->band_eff - 1) / h->band_eff);
-    // steps per launch: the work counter stays below 2^31
+    // steps per launch: the work indices of one launch stay below 2^31
     const int64_t per_launch = std::max<int64_t>(1, ((int64_t)1 << 31) / std::max<int64_t>(1, 2 * items));
     unsigned *sync = h->at<unsigned>(h->L.off_sync);
     ctl.counter = sync;
@@ -1110,8 +1110,10 @@ static int step_impl(lbm_lattice *h, int32_t nsteps, lbm_stream stream)
         cudaError_t e = cudaSuccess;
         if (h->sync_items != items || h->sync_captured) {
             e = cudaMemsetAsync(sync, 0, (size_t)4 * (size_t)(1 + items), s);
-            if (e != cudaSuccess)
+            if (e != cudaSuccess) {
+                h->sync_items = 0;
                 return cuda_fail(e, "work counter reset");
+            }
             h->sync_items = items;
             h->sync_cbase = h->sync_fbase = 0;
         }
