@@ -49,7 +49,7 @@
 // resident warps to cover D.
 //
 // Edge area (arithmetic type C): rows [band][side][rho u_x, rho u_r,
-// T - T0][pitch] for side 0 = the band's first row, 1 = its last, sized for
+// T - T0][epitch] for side 0 = the band's first row, 1 = its last, sized for
 // bands of at least AA_BAND_MIN rows; then columns [strip][side][nr] of
 // rho u_r for side 0 = the strip's first column, 1 = its last (nx - 1 in
 // the last strip).
@@ -190,14 +190,14 @@ __host__ __device__ constexpr int64_t aa_edge_elems(int nr, int pitch, int max_s
 template <class C>
 __device__ __forceinline__ C *edge_row(const StepParams<C> &p, int b, int side, int m)
 {
-    return p.edge + ((int64_t)(b * 2 + side) * 3 + m) * p.pitch + PAD_COLS;
+    return p.edge + ((int64_t)(b * 2 + side) * 3 + m) * p.epitch + PAD_COLS;
 }
 
 // rho u_r of the edge column of strip s, side 0/1, at row 0
 template <class C>
 __device__ __forceinline__ C *edge_col(const StepParams<C> &p, int s, int side)
 {
-    return p.edge + (int64_t)6 * p.pitch * aa_band_cap(p.nr) + (int64_t)(s * 2 + side) * p.nr;
+    return p.edge + (int64_t)6 * p.epitch * aa_band_cap(p.nr) + (int64_t)(s * 2 + side) * p.nr;
 }
 
 // moments of the edge row of band b (side 0/1) for the strip's columns (the density is not needed)

@@ -237,10 +237,11 @@ Layout make_layout(const lbm_desc *d)
     // other, so the rows a warp tile stages lie together in memory (the
     // 4096 x 1024 FP32 jet: 80.0 -> 78.7 us per step; the arithmetic is
     // unchanged, and so are the results).  Every kernel addresses a cell as
-    // q * plane + (j + 1) * pitch + i, so only the strides change.  The
+    // q * plane + (j + 1) * pitch + i, so only the strides change (the AA
+    // edge area keeps rows of one padded row, StepParams::epitch).  The
     // moment-split types keep whole planes (their moment area follows the
-    // last plane), as does the AA pattern (its edge area is sized by rows).
-    if (!is_split(d->storage) && !aa) {
+    // last plane).
+    if (!is_split(d->storage)) {
         L.plane = L.pitch;
         L.pitch *= 13;
     }
@@ -321,6 +322,7 @@ lbm::StepParams<C> make_params(const lbm_lattice *h, const C *u_in, const C *T_i
     p.nx = d.nx;
     p.nr = d.nr;
     p.pitch = h->L.pitch;
+    p.epitch = row_pitch(d.nx);
     p.bc_in = d.bc_in;
     p.bc_out = d.bc_out;
     p.bc_top = d.bc_top;

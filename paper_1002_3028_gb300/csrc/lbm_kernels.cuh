@@ -85,8 +85,10 @@ template <class C>
 struct alignas(16) StepParams {
     const void *src;  // post-collision state of the previous step (with its ghosts)
     void *dst;        // post-collision state written by this step (with its ghosts)
-    int64_t plane;    // elements per population plane ((nr + 2) * pitch)
-    int nx, nr, pitch;
+    int64_t plane;    // elements from one population plane to the next
+    int nx, nr;
+    int pitch;        // elements from one row of a plane to the next (planes interleaved by row:
+                      // 13 padded rows; whole planes: one)
     int bc_in, bc_out, bc_top, bc_bottom, axisym;
     int band;         // rows per warp tile
     int nstrips;      // ceil(nx / (32 NV))
@@ -107,6 +109,7 @@ struct alignas(16) StepParams {
     C *edge;                      // AA layout: moments at the warp tiles' edges (see lbm_aa.cuh)
     int aa;                       // 1: one buffer in the AA layout (src == dst); 0: two buffers
     int phase;                    // AA layout: representation of the stored state
+    int epitch;                   // AA layout: elements per row of the edge area (one padded row)
 };
 
 // ---- storage conversions -----------------------------------------------------
