@@ -44,19 +44,25 @@ def test_desc_struct_matches_header_layout(tmp_path):
     assert got == want
 
 
+def row_elems(nx, size):
+    """Padded row: 32 leading elements, columns 0..nx rounded up to 64, 32 trailing elements,
+    and for 4- and 8-byte values one 128-byte block more if the row would hold an even number
+    of them."""
+    row = 32 + (nx + 1 + 63) // 64 * 64 + 32
+    return row + (128 // size if size >= 4 and (row * size // 128) % 2 == 0 else 0)
+
+
 def test_required_bytes_counts_two_buffers():
-    """Two buffers of 13 planes; each plane has ghost rows -1 and nr and a
-    padded row pitch (32 leading elements, columns 0..nx rounded up to 64,
-    32 trailing elements)."""
+    """Two buffers of 13 planes; each plane has ghost rows -1 and nr and padded rows."""
     cfg = I.LatticeConfig(nx=100, nr=40)
-    pitch = 32 + 128 + 32
+    assert [row_elems(100, sz) for sz in (8, 4, 2)] == [208, 224, 192]
     for st, sz in (("f64", 8), ("f32", 4), ("f16", 2), ("bf16", 2)):
         n = lbm.required_bytes(cfg, st)
-        two = 2 * 13 * pitch * (40 + 2) * sz
+        two = 2 * 13 * row_elems(100, sz) * (40 + 2) * sz
         assert two <= n < two + 200_000
     for st in ("f16s", "bf16s"):  # 13 two-byte planes and 3 FP32 moment planes per buffer
         n = lbm.required_bytes(cfg, st)
-        two = 2 * (13 * 2 + 3 * 4) * pitch * (40 + 2)
+        two = 2 * (13 * 2 + 3 * 4) * row_elems(100, 2) * (40 + 2)
         assert two <= n < two + 200_000
 
 
