@@ -8,10 +8,14 @@ kernel (tiles of step t + 1 start as soon as their neighbours finished
 step t).  The two population buffers
 (436 MB in FP32) are larger than the 129 MB L2, so no flush is needed
 between steps.  ``--workload ensemble`` steps 256 ragged jets as one batch
-(persistent multi-step launches, CUDA-graph replay); ``--workload jetNXxNR`` any size.
+(persistent multi-step launches, CUDA-graph replay); ``--workload jetNXxNR`` any size;
+``--workload serving`` the continuous-batching service alone; ``--workload sweep`` the
+precision sweep (every storage type against an FP64 GPU run of the same steps).
 
-Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle on the host cores on the same workload instead.
+Prints one JSON line (rank 0).  The default line also carries the ensemble (FP16
+moment-split and rest-deviation storage) and the 2000-request serving run against the
+one-at-a-time FP32 path (``--no-extras`` leaves them out).  ``--impl reference`` times the
+FP64 CPU oracle on the host cores on the same workload instead.
 """
 from __future__ import annotations
 
