@@ -14,9 +14,8 @@ with a strongly temperature-dependent viscosity.
 """
 from __future__ import annotations
 
-import dataclasses
 import math
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 from typing import List, Optional
 
 import numpy as np

@@ -11,7 +11,6 @@ import ctypes as C
 import os
 import re
 import threading
-from typing import Optional
 
 import numpy as np
 

@@ -16,10 +16,9 @@ runs against the GPU engine here and against a fake engine in the CPU tests.
 from __future__ import annotations
 
 import collections
-import dataclasses
 import time
-from dataclasses import dataclass, field
-from typing import Callable, Dict, List, Optional
+from dataclasses import dataclass
+from typing import Callable, Dict, List
 
 import numpy as np
 

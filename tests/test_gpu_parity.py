@@ -26,7 +26,6 @@ over its thermal relaxation time.  Moment-split storage keeps j and T in
 FP32 and rounds only the deviations from the linear equilibrium.
 Turbulent runs are compared one step at a time from an identical state.
 """
-import dataclasses
 import os
 
 import numpy as np

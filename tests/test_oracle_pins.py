@@ -7,7 +7,6 @@ numerical solve of Eq. 3, closed-form flows of the axisymmetric equations
 pressure drop), symmetry and conservation invariants, and hand-worked
 boundary cases on tiny lattices.
 """
-import dataclasses
 import math
 import os
 
