@@ -4,7 +4,9 @@ Times each candidate shape on the live lattice or batch with CUDA events on
 its stream (after a warm-up), three runs each, keeps the one whose slowest
 run is fastest, and remembers it in a small
 JSON cache keyed by the GPU name, the storage type and the lattice shape(s),
-so a later lattice of the same kind starts from the tuned shape.  The tile
+so a later lattice of the same kind starts from the tuned shape.  The key
+also holds the memory pattern: the in-place (AA) kernel takes other strip
+widths and bands than the two-buffer one.  The tile
 is the warp's strip of 32 or 64 columns (one or two nodes per lane) by the
 band height; results are bit for bit the same for every shape.  Tuning steps
 the lattice: tune before setting the initial state, or save and restore it
@@ -61,10 +63,10 @@ def _store(key: str, value) -> None:
         os.replace(tmp, CACHE)
 
 
-def lattice_key(storage: str, shapes: Iterable[Tuple[int, int]]) -> str:
+def lattice_key(storage: str, shapes: Iterable[Tuple[int, int]], pattern: str = "ab") -> str:
     shapes = sorted(shapes)
     digest = hashlib.sha1(repr(shapes).encode()).hexdigest()[:12]
-    return f"{_gpu_name()}|{storage}|{len(shapes)}|{digest}"
+    return f"{_gpu_name()}|{storage}|{pattern}|{len(shapes)}|{digest}"
 
 
 def _time(step_fn, steps: int, warmup: int) -> float:
@@ -98,7 +100,8 @@ def tune(target, candidates: Optional[Sequence[Tuple[int, int, int]]] = None, st
     """Pick and set the fastest (strip columns, band rows, warps per CTA) for a Lattice or Batch.
 
     Returns the chosen shape.  With use_cache, a shape tuned earlier for the
-    same GPU, storage and lattice shapes is applied without timing.  Each
+    same GPU, storage type, memory pattern and lattice shapes is applied
+    without timing.  Each
     candidate runs `steps` steps in one persistent launch (enough that the
     launch's ramp and tail do not decide the ranking), three times, and is
     ranked by its slowest run.  Candidates with a strip width the lattice
@@ -110,7 +113,7 @@ def tune(target, candidates: Optional[Sequence[Tuple[int, int, int]]] = None, st
     members = target.members if is_batch else [target]
     shapes = [(m.nx, m.nr) for m in members]
     pattern = members[0].pattern if members else "ab"
-    key = lattice_key(target.storage, shapes)
+    key = lattice_key(target.storage, shapes, pattern)
     if use_cache:
         hit = _load().get(key)
         if hit:

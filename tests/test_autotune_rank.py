@@ -71,3 +71,14 @@ def test_fp64_takes_only_32_column_strips(tuner, monkeypatch):
     other.storage = "f64"
     with pytest.raises(ValueError):  # no candidate of a width FP64 accepts
         tuner.tune(other, candidates=[(64, 4, 1)], use_cache=False)
+
+
+def test_the_cache_keeps_the_two_memory_patterns_apart(tuner, monkeypatch):
+    ab = FakeLattice()
+    monkeypatch.setattr(tuner, "_time", lambda run, steps, warmup: 0.05 if ab.shape[0] == 32 else 0.06)
+    assert tuner.tune(ab, candidates=[(64, 4, 1), (32, 8, 1)], steps=10, warmup=2) == (32, 8, 1)
+    aa = FakeLattice()  # same storage and shape, one buffer updated in place: 64-column strips only
+    aa.pattern = "aa"
+    monkeypatch.setattr(tuner, "_time", lambda run, steps, warmup: 0.07)
+    assert tuner.tune(aa, candidates=[(64, 4, 1), (32, 8, 1)], steps=10, warmup=2) == (64, 4, 1)
+    assert len(json.load(open(tuner.CACHE))) == 2
