@@ -129,8 +129,9 @@ int strip_cols(int storage) { return storage == LBM_F64 ? 32 : 64; }
 int default_nv(int storage) { return storage == LBM_F64 ? 1 : 2; }
 
 // ... and of a batch: moment-split batches default to 32-column strips (the ragged 256-jet
-// ensemble in FP16 moment-split storage: 721 against 832 us per step at 64 columns; the
-// rest-deviation FP16 batch is faster at 64, 377 against 392 us)
+// ensemble in FP16 moment-split storage at band 64: 588 against 678 us per step at 64
+// columns, whose 162-register tiles leave 12 warps per SM; the rest-deviation FP16 batch is
+// faster at 64, 377 against 392 us)
 int batch_default_nv(int storage) { return is_split(storage) ? 1 : default_nv(storage); }
 
 size_t storage_bytes(int storage)
