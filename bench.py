@@ -103,11 +103,14 @@ def kernel_hash(pattern: str = "ab") -> str:
     return hashlib.sha256("\n".join(code).encode()).hexdigest()[:16]
 
 
-def ncu_traffic(storage: str, workload: str, pattern: str = "ab"):
-    """DRAM bytes per step of the step kernel (a launch holds K steps; per step, like
-    `achieved`) from the committed ncu summary, or None if there is none for this
-    storage/workload/pattern or the kernel source changed since."""
-    name = f"step_kernel_{storage}_{workload}.md" if pattern == "ab" else f"aa_step_kernel_{storage}_{workload}.md"
+def ncu_traffic(storage: str, workload: str, pattern: str = "ab", kernel: str = "step"):
+    """DRAM bytes per step of the step kernel (or, with kernel="batch", of the batch kernel;
+    a launch holds K steps; per step, like `achieved`) from the committed ncu summary, or None
+    if there is none for this storage/workload/pattern or the kernel source changed since."""
+    if kernel == "batch":
+        name = f"batch_kernel_{storage}_{workload}.md"
+    else:
+        name = f"step_kernel_{storage}_{workload}.md" if pattern == "ab" else f"aa_step_kernel_{storage}_{workload}.md"
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
@@ -573,7 +576,8 @@ def ensemble_object(device, storage: str = "f16s", steps: int = 5000, warm: int 
             "launch": dict(zip(("band_rows", "warps_per_cta", "tiles"), launch)),
             "graph": "one captured launch of 64 steps, replayed",
             "roofline": {"bound": "hbm", "bytes_per_lup": bytes_per_lup(storage), "achieved": achieved,
-                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind},
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": ncu_traffic(storage, f"ensemble{count}", kernel="batch") if count == 256 else None},
             "error_vs_f64": {"lattices": len(picks), "per_step": worst(errs, "per_step"),
                              "after_1000_steps": {k: worst(errs, "after_steps." + k)
                                                   for k in errs[0]["after_steps"]}},

@@ -32,6 +32,15 @@ def test_committed_ncu_summaries_belong_to_the_current_kernel(storage, pattern):
     assert t is not None and 0.9 * bench.bytes_per_lup(storage) * 4096 * 1024 < t
 
 
+def test_committed_batch_summary_belongs_to_the_current_kernel():
+    """The ensemble's traffic figure: DRAM bytes per step of the 256-jet batch in moment-split
+    storage, from a capture of the kernel code as it is."""
+    t = bench.ncu_traffic("f16s", "ensemble256", kernel="batch")
+    nodes = 23162880  # the seeded 256-jet ensemble
+    assert t is not None and bench.bytes_per_lup("f16s") * nodes < t
+    assert bench.ncu_traffic("f16", "ensemble256", kernel="batch") is None  # no summary: null
+
+
 def test_kernel_hash_of_the_aa_pattern_covers_its_own_source():
     assert bench.kernel_hash("aa") != bench.kernel_hash("ab")
 
